@@ -1,0 +1,199 @@
+/*
+ * hf.h -- C ABI of the GB300 Hilbert-forest library (libhf.so).
+ *
+ * The library implements the data-parallel path of the Hilbert forest
+ * (Imamura et al., "Hilbert Forest in the SISAP 2025 Indexing Challenge",
+ * arXiv 2508.21682): for each of T trees a seeded permutation and reflection
+ * of the coordinate axes, b-bit quantization, the Hilbert key of every point,
+ * a sort by that key, squared distances between points within w positions of
+ * each other in the order, and a per-point top-k merge that yields an
+ * approximate kNN graph; queries are located in the same orders by binary
+ * search and answered from the windows around their positions.
+ *
+ * Conventions (the paper fixes none of these):
+ *   - curve: Skilling's transposed Hilbert index (AIP Conf. Proc. 707, 2004);
+ *     key bit l*d+i, counted from the most significant end, is bit (b-1-l) of
+ *     the transformed coordinate i; keys are W = ceil(d*b/64) 64-bit words,
+ *     word 0 most significant, zero-padded at the low end;
+ *   - quantization: per-axis lo = min, hi = max of the data;
+ *     scale = (float)(2^b / (double)(float)(hi - lo)) (0 for a flat axis);
+ *     code = clamp(floor(fl32(fl32(x - lo) * scale)), 0, 2^b - 1);
+ *   - tree t: splitmix64 from state seed + (t+1)*0x9E3779B97F4A7C15; a
+ *     Fisher-Yates shuffle (j = d-1 .. 1, m = next() % (j+1)) gives pi, then
+ *     r[j] = next() >> 63; permuted coordinate j is code[pi[j]], replaced by
+ *     2^b - 1 - code when r[j] = 1;
+ *   - order: ascending (full key, point index);
+ *   - graph window: positions p +- delta, 1 <= delta <= w, clipped, no wrap;
+ *   - search window: positions [p - w, p + w) around the query's lower-bound
+ *     position p, clipped;
+ *   - distance: squared Euclidean in float32 with exact coordinate
+ *     differences; lists ascending by (distance, index); candidate sets are
+ *     sets (a point appears once per list, never in its own list); unfilled
+ *     slots are (index -1, distance +inf).
+ *
+ * Memory: every pointer argument may be device memory or host memory; the
+ * library checks with cudaPointerGetAttributes. Host inputs are copied to the
+ * device inside the call and host outputs are copied back before it returns,
+ * on the given stream. Device inputs are read in place.
+ *
+ * Synchronisation: every call that takes a stream enqueues its work on that
+ * stream (NULL = the legacy default stream), then synchronises the stream,
+ * reads the library's device error word and returns a status. No call aborts
+ * the process or traps on the device.
+ *
+ * Errors: HF_EINVAL for bad arguments (checked before any work), HF_ENOMEM
+ * when a device allocation fails, HF_ECUDA for any other CUDA error,
+ * HF_ENONFINITE when the data or a query holds NaN or +-inf, HF_ETIMEOUT when
+ * a bounded inter-block wait inside the sort gave up, HF_ESTATE when a call
+ * needs state the forest does not hold. On error, outputs are unspecified.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hf_forest hf_forest; /* opaque; owned by the library */
+
+enum {
+  HF_OK = 0,
+  HF_EINVAL = -1,
+  HF_ENOMEM = -2,
+  HF_ECUDA = -3,
+  HF_ENONFINITE = -4,
+  HF_ETIMEOUT = -5,
+  HF_ESTATE = -6,
+  HF_ENOTIMPL = -7
+};
+
+/* Limits checked by every entry point. */
+#define HF_MAX_D 4096
+#define HF_MAX_BITS 8
+#define HF_MAX_K 64
+#define HF_MAX_N (((int64_t)1 << 30) - 1)
+
+/*
+ * hf_build -- preprocessing and the per-tree orders.
+ * Paper: Algorithm 2, "randomly permute coordinate axes" and "compute Hilbert
+ * order of all points" for each sort; Algorithm 1, "Build n Hilbert trees with
+ * randomized axis orders"; Section 2 (Hilbert sort, Hilbert tree as the
+ * sorted sequence that binary search runs on).
+ *
+ * points : n x d float32, row-major (point i at points + i*d). Borrowed when
+ *          it is device memory: it is never written and must stay valid and
+ *          unchanged until hf_free, because hf_knn_graph and hf_search read it.
+ *          When it is host memory the forest keeps its own device copy.
+ * n      : number of points, 2 <= n <= HF_MAX_N.
+ * d      : dimension, 1 <= d <= HF_MAX_D.
+ * T      : number of trees (sorts), T >= 1.
+ * bits   : bits per coordinate for the key, 1 <= bits <= HF_MAX_BITS.
+ * seed   : seed of the per-tree axis permutations and reflections.
+ * stream : cudaStream_t (as void*), or NULL.
+ * out    : receives the new forest; set to NULL on error.
+ * The forest keeps, per tree, the order (sigma: position -> point) and the
+ * sorted key prefixes, so that hf_search can run later.
+ */
+int hf_build(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits,
+             uint64_t seed, void* stream, hf_forest** out);
+
+/*
+ * hf_build_opts -- hf_build with build options, a comma-separated list of
+ * key=value pairs (NULL or "" = defaults):
+ *   prefix_words=K   64-bit key words sorted by radix (1..W, default min(2, W));
+ *                    runs of equal prefixes are then ordered by the full key;
+ *   spin_limit_us=U  bound of each inter-block wait in the sort (default 2e6);
+ *   test_stall=1     test hook: one block of the first sort pass waits on a
+ *                    status word that nothing writes, so the bounded wait runs
+ *                    out and the call returns HF_ETIMEOUT.
+ * Unknown keys give HF_EINVAL.
+ */
+int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits,
+                  uint64_t seed, const char* options, void* stream, hf_forest** out);
+
+/*
+ * hf_knn_graph -- approximate kNN graph (Algorithm 2 first stage and final
+ * selection; the sketch stage is not part of this path).
+ * For every point, the candidates are the points within w positions of it in
+ * any tree's order; the result is the k nearest candidates by float32 squared
+ * distance, ascending by (distance, index).
+ * k        : 1 <= k <= HF_MAX_K.
+ * w        : window half-width, w >= 1.
+ * out_idx  : n x k int32 (row i = neighbours of point i); -1 in unfilled slots.
+ * out_dist : n x k float32 squared distances; +inf in unfilled slots.
+ */
+int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist,
+                 void* stream);
+
+/*
+ * hf_search -- batched query search (Algorithm 1 first stage and final
+ * selection; Section 2: binary search locates a point in a Hilbert order).
+ * Queries are quantized with the data's lo/scale (clamped); in each tree the
+ * query's position p is the lower bound of its full key among the data keys;
+ * the candidates are the points at positions [p - w, p + w); the result is the
+ * k nearest of their union by float32 squared distance.
+ * queries  : nq x d float32, row-major; nq >= 0 (0 returns HF_OK at once).
+ * out_idx  : nq x k int32; out_dist : nq x k float32.
+ */
+int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
+              int32_t* out_idx, float* out_dist, void* stream);
+
+/* hf_free -- releases the forest and everything it owns (NULL is a no-op). */
+int hf_free(hf_forest* f);
+
+/* hf_status_string -- static text for a status code (never NULL). */
+const char* hf_status_string(int status);
+
+/*
+ * hf_set_option -- per-forest run-time options for later calls:
+ *   mode=0  plain float32 window distances (default);
+ *   timing=1  record per-phase CUDA-event timings (default 1).
+ * Unknown keys or values give HF_EINVAL.
+ */
+int hf_set_option(hf_forest* f, const char* key, int64_t value);
+
+/*
+ * hf_get_timings -- milliseconds of the last calls' phases, in this order:
+ * [0] quantize, [1] keys, [2] sort, [3] tie fix-up, [4] window+merge,
+ * [5] search, [6] keys+sort launches count (as float). Writes min(cap, 7).
+ */
+int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
+
+/* hf_info -- n, d, T, bits, W (key words), K (prefix words) into out[0..5]. */
+int hf_info(const hf_forest* f, int64_t* out, int32_t cap);
+
+/*
+ * hf_tree_params -- host-only: the axis permutation pi[d] and reflection bits
+ * r[d] of tree `tree` for `seed` (conventions above). Host pointers only.
+ */
+int hf_tree_params(uint64_t seed, int32_t tree, int32_t d, int32_t* pi, uint8_t* r);
+
+/* ---- inspection exports (tests and tools) -------------------------------- */
+
+/* Quantized codes, n x d uint8, point order. */
+int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream);
+
+/* Full keys of tree t, n x W uint64 (row i = point i, word 0 first). */
+int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream);
+
+/* Order of tree t: sigma[p] = point at position p, n uint32. */
+int hf_debug_order(hf_forest* f, int32_t tree, uint32_t* out_sigma, void* stream);
+
+/* Lower-bound positions of nq queries in tree t, nq int64. */
+int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq,
+                    int64_t* out_pos, void* stream);
+
+/*
+ * Full keys of raw codes with the identity permutation and no reflection:
+ * codes n x d uint8 (values < 2^bits), out n x W uint64. n >= 1.
+ */
+int hf_debug_keys_from_codes(const uint8_t* codes, int64_t n, int32_t d, int32_t bits,
+                             uint64_t* out_keys, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

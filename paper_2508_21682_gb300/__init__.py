@@ -1,0 +1,238 @@
+"""Python binding of libhf.so, the GB300 Hilbert-forest library.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA
+tensors are passed by device pointer together with torch's current stream,
+host arrays by host pointer (the library copies them). The library must have
+been built (``__graft_entry__.build()``); importing this package without it
+raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhf.so")
+
+HF_OK = 0
+HF_EINVAL = -1
+HF_ENOMEM = -2
+HF_ECUDA = -3
+HF_ENONFINITE = -4
+HF_ETIMEOUT = -5
+HF_ESTATE = -6
+HF_ENOTIMPL = -7
+
+SYMBOLS = [
+    "hf_build", "hf_build_opts", "hf_knn_graph", "hf_search", "hf_free", "hf_status_string",
+    "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
+    "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
+]
+
+_lib = None
+
+
+class HFError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libhf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhf.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "hf_build": [vp, i64, i32, i32, i32, u64, vp, pp],
+        "hf_build_opts": [vp, i64, i32, i32, i32, u64, ctypes.c_char_p, vp, pp],
+        "hf_knn_graph": [vp, i32, i32, vp, vp, vp],
+        "hf_search": [vp, vp, i64, i32, i32, vp, vp, vp],
+        "hf_free": [vp],
+        "hf_status_string": [ctypes.c_int],
+        "hf_set_option": [vp, ctypes.c_char_p, i64],
+        "hf_get_timings": [vp, vp, i32],
+        "hf_info": [vp, vp, i32],
+        "hf_tree_params": [u64, i32, i32, vp, vp],
+        "hf_debug_codes": [vp, vp, vp],
+        "hf_debug_keys": [vp, i32, vp, vp],
+        "hf_debug_order": [vp, i32, vp, vp],
+        "hf_debug_locate": [vp, i32, vp, i64, vp, vp],
+        "hf_debug_keys_from_codes": [vp, i64, i32, i32, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "hf_status_string" else ctypes.c_int
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return lib().hf_status_string(status).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != HF_OK:
+        raise HFError(rc, what)
+
+
+def _ptr(a):
+    """(pointer, keepalive) of a contiguous torch tensor or numpy array."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, a
+    import torch  # noqa: F401  (torch tensors only)
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), a
+
+
+def _stream(*arrays):
+    """torch's current stream when any argument is a CUDA tensor, else NULL."""
+    for a in arrays:
+        if a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False):
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def tree_params(seed: int, tree: int, d: int):
+    """Host-only: (pi int32[d], r uint8[d]) of a tree."""
+    pi = np.empty(d, np.int32)
+    r = np.empty(d, np.uint8)
+    _check(lib().hf_tree_params(seed, tree, d, pi.ctypes.data, r.ctypes.data), "hf_tree_params")
+    return pi, r
+
+
+def keys_from_codes(codes, bits: int, out=None):
+    """Full keys (n x W uint64) of raw codes (n x d uint8), identity order."""
+    n, d = codes.shape
+    W = (d * bits + 63) // 64
+    if out is None:
+        out = _empty_like_input(codes, (n, W), "uint64")
+    cp, _k1 = _ptr(codes)
+    op, _k2 = _ptr(out)
+    _check(lib().hf_debug_keys_from_codes(cp, n, d, bits, op, _stream(codes, out)), "hf_debug_keys_from_codes")
+    return out
+
+
+def _empty_like_input(ref, shape, dtype):
+    if isinstance(ref, np.ndarray):
+        return np.empty(shape, dtype=dtype)
+    import torch
+    tdt = {"uint64": torch.int64, "int32": torch.int32, "float32": torch.float32,
+           "uint32": torch.int32, "int64": torch.int64, "uint8": torch.uint8}[dtype]
+    return torch.empty(shape, dtype=tdt, device=ref.device)
+
+
+class Forest:
+    """A built Hilbert forest (hf_build). Holds the library handle."""
+
+    def __init__(self, points, T: int, bits: int = 8, seed: int = 3, options: str | None = None):
+        n, d = points.shape
+        self.n, self.d, self.T, self.bits = int(n), int(d), int(T), int(bits)
+        self._points = points  # the library borrows device memory: keep it alive
+        p, _ = _ptr(points)
+        h = ctypes.c_void_p()
+        st = _stream(points)
+        if options is None:
+            rc = lib().hf_build(p, n, d, T, bits, seed, st, ctypes.byref(h))
+        else:
+            rc = lib().hf_build_opts(p, n, d, T, bits, seed, options.encode(), st, ctypes.byref(h))
+        _check(rc, "hf_build")
+        self._h = h
+        info = np.zeros(6, np.int64)
+        lib().hf_info(self._h, info.ctypes.data, 6)
+        self.W, self.K = int(info[4]), int(info[5])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def knn_graph(self, k: int, w: int, out_idx=None, out_dist=None):
+        """(idx int32[n, k], dist float32[n, k]); outputs default to the
+        points' kind (CUDA tensors for CUDA points, numpy otherwise)."""
+        if out_idx is None:
+            out_idx = _empty_like_input(self._points, (self.n, k), "int32")
+        if out_dist is None:
+            out_dist = _empty_like_input(self._points, (self.n, k), "float32")
+        ip, _a = _ptr(out_idx)
+        dp, _b = _ptr(out_dist)
+        _check(lib().hf_knn_graph(self._h, k, w, ip, dp, _stream(out_idx, out_dist, self._points)),
+               "hf_knn_graph")
+        return out_idx, out_dist
+
+    def search(self, queries, k: int, w: int, out_idx=None, out_dist=None):
+        nq = queries.shape[0]
+        if out_idx is None:
+            out_idx = _empty_like_input(queries, (nq, k), "int32")
+        if out_dist is None:
+            out_dist = _empty_like_input(queries, (nq, k), "float32")
+        qp, _q = _ptr(queries)
+        ip, _a = _ptr(out_idx)
+        dp, _b = _ptr(out_dist)
+        _check(lib().hf_search(self._h, qp, nq, k, w, ip, dp, _stream(queries, out_idx, out_dist)),
+               "hf_search")
+        return out_idx, out_dist
+
+    def set_option(self, key: str, value: int):
+        _check(lib().hf_set_option(self._h, key.encode(), value), "hf_set_option")
+
+    def timings(self):
+        t = np.zeros(7, np.float32)
+        lib().hf_get_timings(self._h, t.ctypes.data, 7)
+        names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches"]
+        return dict(zip(names, t.tolist()))
+
+    # ---- inspection --------------------------------------------------------
+    def codes(self):
+        out = np.empty((self.n, self.d), np.uint8)
+        _check(lib().hf_debug_codes(self._h, out.ctypes.data, None), "hf_debug_codes")
+        return out
+
+    def keys(self, tree: int):
+        out = np.empty((self.n, self.W), np.uint64)
+        _check(lib().hf_debug_keys(self._h, tree, out.ctypes.data, None), "hf_debug_keys")
+        return out
+
+    def order(self, tree: int):
+        out = np.empty(self.n, np.uint32)
+        _check(lib().hf_debug_order(self._h, tree, out.ctypes.data, None), "hf_debug_order")
+        return out
+
+    def locate(self, tree: int, queries):
+        nq = queries.shape[0]
+        out = np.empty(nq, np.int64)
+        qp, _q = _ptr(queries)
+        _check(lib().hf_debug_locate(self._h, tree, qp, nq, out.ctypes.data, _stream(queries)),
+               "hf_debug_locate")
+        return out
+
+
+def build(points, T: int, bits: int = 8, seed: int = 3, options: str | None = None) -> Forest:
+    return Forest(points, T, bits, seed, options)

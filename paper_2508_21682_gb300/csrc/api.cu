@@ -1,0 +1,553 @@
+// C-ABI entry points and the host runtime around the kernels: argument
+// checks, host/device buffer resolution, the forest's allocations, the
+// per-tree loop, the device error word and per-phase CUDA-event timings.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "hf_internal.cuh"
+
+size_t sort_status_words(int64_t n, int K);
+int tie_small_cap(int W, int d);
+
+namespace {
+
+constexpr uint64_t GOLDEN_GAMMA = 0x9E3779B97F4A7C15ull;
+
+uint64_t splitmix64_next(uint64_t& state) {
+  state += GOLDEN_GAMMA;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// 1: device-accessible, 0: host memory, -1: error
+int classify(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(reinterpret_cast<void*>(p));
+  p = nullptr;
+}
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return HF_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA;
+}
+
+// Synchronises, reads and clears the error word, maps to a status.
+int finish(hf_forest* f, cudaStream_t s) {
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_cuda(e);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return map_cuda(e);
+  int word = 0;
+  if (cudaMemcpy(&word, f->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HF_ECUDA;
+  if (word) cudaMemset(f->err, 0, sizeof(int));
+  if (word & HF_ERRBIT_NONFINITE) return HF_ENONFINITE;
+  if (word & HF_ERRBIT_TIMEOUT) return HF_ETIMEOUT;
+  return HF_OK;
+}
+
+void free_build_scratch(hf_forest* f) {
+  dfree(f->pk);
+  dfree(f->sort.keys_a);
+  dfree(f->sort.keys_b);
+  dfree(f->sort.vals_a);
+  dfree(f->sort.vals_b);
+  dfree(f->sort.status);
+  dfree(f->sort.hist);
+  dfree(f->tie.runs);
+  dfree(f->tie.big_runs);
+  dfree(f->tie.counters);
+}
+
+void destroy(hf_forest* f) {
+  if (!f) return;
+  free_build_scratch(f);
+  dfree(f->x_owned);
+  dfree(f->lo);
+  dfree(f->scale);
+  dfree(f->planes);
+  dfree(f->pi);
+  dfree(f->rbits);
+  dfree(f->prefix);
+  dfree(f->sigma);
+  dfree(f->err);
+  for (auto& e : f->ev)
+    if (e) cudaEventDestroy(e);
+  delete f;
+}
+
+int parse_options(hf_forest* f, const char* opts) {
+  if (!opts) return HF_OK;
+  std::string s(opts);
+  size_t i = 0;
+  while (i < s.size()) {
+    size_t j = s.find(',', i);
+    if (j == std::string::npos) j = s.size();
+    std::string kv = s.substr(i, j - i);
+    i = j + 1;
+    if (kv.empty()) continue;
+    size_t eq = kv.find('=');
+    if (eq == std::string::npos) return HF_EINVAL;
+    std::string key = kv.substr(0, eq), val = kv.substr(eq + 1);
+    char* end = nullptr;
+    long long v = strtoll(val.c_str(), &end, 10);
+    if (end == val.c_str() || *end) return HF_EINVAL;
+    if (key == "prefix_words") {
+      if (v < 1 || v > 8) return HF_EINVAL;
+      f->K = (int)v;
+    } else if (key == "spin_limit_us") {
+      if (v < 1) return HF_EINVAL;
+      f->spin_limit_us = v;
+    } else if (key == "test_stall") {
+      f->test_stall = v ? 1 : 0;
+    } else {
+      return HF_EINVAL;
+    }
+  }
+  return HF_OK;
+}
+
+struct Timer {
+  hf_forest* f;
+  cudaStream_t s;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[8];
+  explicit Timer(hf_forest* ff, cudaStream_t ss) : f(ff), s(ss) {}
+  cudaEvent_t mark() {
+    cudaEvent_t e = nullptr;
+    if (f->timing) {
+      cudaEventCreate(&e);
+      cudaEventRecord(e, s);
+    }
+    return e;
+  }
+  void span(int slot, cudaEvent_t a, cudaEvent_t b) {
+    if (a && b) spans[slot].push_back({a, b});
+  }
+  // after a sync
+  void collect(std::initializer_list<int> slots) {
+    for (int sl : slots) {
+      float tot = 0.f;
+      for (auto& p : spans[sl]) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.first, p.second);
+        tot += ms;
+      }
+      if (!spans[sl].empty()) f->timings[sl] = tot;
+    }
+  }
+  ~Timer() {
+    for (auto& v : spans)
+      for (auto& p : v) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+  }
+};
+
+}  // namespace
+
+void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r) {
+  uint64_t state = seed + (uint64_t)(tree + 1) * GOLDEN_GAMMA;
+  for (int j = 0; j < d; ++j) pi[j] = j;
+  for (int j = d - 1; j >= 1; --j) {
+    const uint64_t m = splitmix64_next(state) % (uint64_t)(j + 1);
+    const int32_t tmp = pi[j];
+    pi[j] = pi[m];
+    pi[m] = tmp;
+  }
+  for (int j = 0; j < d; ++j) r[j] = (uint8_t)(splitmix64_next(state) >> 63);
+}
+
+extern "C" {
+
+const char* hf_status_string(int status) {
+  switch (status) {
+    case HF_OK: return "ok";
+    case HF_EINVAL: return "invalid argument";
+    case HF_ENOMEM: return "device allocation failed";
+    case HF_ECUDA: return "CUDA error";
+    case HF_ENONFINITE: return "non-finite input value";
+    case HF_ETIMEOUT: return "bounded wait between blocks timed out";
+    case HF_ESTATE: return "forest does not hold the needed state";
+    case HF_ENOTIMPL: return "not implemented for these arguments";
+    default: return "unknown status";
+  }
+}
+
+int hf_tree_params(uint64_t seed, int32_t tree, int32_t d, int32_t* pi, uint8_t* r) {
+  if (!pi || !r || d < 1 || d > HF_MAX_D || tree < 0) return HF_EINVAL;
+  hf_tree_params_host(seed, tree, d, pi, r);
+  return HF_OK;
+}
+
+int hf_build(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits, uint64_t seed,
+             void* stream, hf_forest** out) {
+  return hf_build_opts(points, n, d, T, bits, seed, nullptr, stream, out);
+}
+
+int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits, uint64_t seed,
+                  const char* options, void* stream, hf_forest** out) {
+  if (out) *out = nullptr;
+  if (!points || !out || n < 2 || n > HF_MAX_N || d < 1 || d > HF_MAX_D || T < 1 || bits < 1 ||
+      bits > HF_MAX_BITS)
+    return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hf_forest* f = new hf_forest();
+  f->n = n;
+  f->d = d;
+  f->T = T;
+  f->bits = bits;
+  f->seed = seed;
+  f->W = (int)(((int64_t)d * bits + 63) / 64);
+  f->W32 = (d + 31) / 32;
+  f->K = f->W < 2 ? f->W : 2;
+  int rc = parse_options(f, options);
+  if (rc == HF_OK && f->K > f->W) rc = HF_EINVAL;
+  if (rc != HF_OK) {
+    delete f;
+    return rc;
+  }
+  {
+    const int64_t need = ((int64_t)64 * f->K + d - 1) / d;
+    f->L = (int)(need < bits ? need : bits);
+  }
+  cudaGetDevice(&f->device);
+
+  Timer tm(f, s);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  const int dev = classify(points);
+  if (dev == 1) {
+    f->x = points;
+  } else {
+    chk(dalloc(&f->x_owned, (size_t)n * d));
+    if (e == cudaSuccess)
+      chk(cudaMemcpyAsync(f->x_owned, points, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, s));
+    f->x = f->x_owned;
+  }
+  const int K = f->K, W32 = f->W32;
+  chk(dalloc(&f->lo, d));
+  chk(dalloc(&f->scale, d));
+  chk(dalloc(&f->planes, (size_t)bits * n * W32));
+  chk(dalloc(&f->pi, (size_t)T * d));
+  chk(dalloc(&f->rbits, (size_t)T * W32));
+  chk(dalloc(&f->prefix, (size_t)T * K * n));
+  chk(dalloc(&f->sigma, (size_t)T * n));
+  chk(dalloc(&f->err, 1));
+  chk(dalloc(&f->pk, (size_t)K * n));
+  chk(dalloc(&f->sort.keys_a, n));
+  chk(dalloc(&f->sort.keys_b, n));
+  chk(dalloc(&f->sort.vals_a, n));
+  chk(dalloc(&f->sort.vals_b, n));
+  chk(dalloc(&f->sort.status, sort_status_words(n, K)));
+  chk(dalloc(&f->sort.hist, (size_t)K * 8 * 256));
+  const int cap = tie_small_cap(f->W, d);
+  f->tie.big_cap = n / (cap + 1) + 1;
+  chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1)));
+  chk(dalloc(&f->tie.big_runs, (size_t)T * f->tie.big_cap));
+  chk(dalloc(&f->tie.counters, (size_t)T * 4));
+  void* rscratch = nullptr;
+  const size_t rbytes = range_scratch_bytes(n, d);
+  chk(cudaMalloc(&rscratch, rbytes));
+  if (e != cudaSuccess) {
+    cudaFree(rscratch);
+    destroy(f);
+    return map_cuda(e);
+  }
+  cudaMemsetAsync(f->err, 0, sizeof(int), s);
+
+  // per-tree permutations and reflection masks (host, then one upload)
+  std::vector<int32_t> hpi((size_t)T * d);
+  std::vector<uint32_t> hr((size_t)T * W32, 0u);
+  std::vector<uint8_t> r(d);
+  for (int t = 0; t < T; ++t) {
+    hf_tree_params_host(seed, t, d, hpi.data() + (size_t)t * d, r.data());
+    for (int j = 0; j < d; ++j)
+      if (r[j]) hr[(size_t)t * W32 + (j >> 5)] |= 1u << (j & 31);
+  }
+  cudaMemcpyAsync(f->pi, hpi.data(), hpi.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(f->rbits, hr.data(), hr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+
+  cudaEvent_t a0 = tm.mark();
+  launch_range(f->x, n, d, f->lo, f->scale, bits, f->err, rscratch, rbytes, s);
+  launch_quantize_planes(f->x, n, d, f->lo, f->scale, bits, f->planes, f->err, s);
+  cudaEvent_t a1 = tm.mark();
+  tm.span(0, a0, a1);
+  for (int t = 0; t < T && rc == HF_OK; ++t) {
+    cudaEvent_t k0 = tm.mark();
+    launch_prefix_keys(f->planes, n, d, bits, K, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32, f->pk, s);
+    cudaEvent_t k1 = tm.mark();
+    rc = sort_tree(f, t, s);
+    cudaEvent_t k2 = tm.mark();
+    tm.span(1, k0, k1);
+    tm.span(2, k1, k2);
+  }
+  if (rc == HF_OK) rc = finish(f, s);
+  // runs of equal prefixes longer than the on-device cap
+  if (rc == HF_OK) {
+    std::vector<uint32_t> ctr((size_t)T * 4);
+    if (cudaMemcpy(ctr.data(), f->tie.counters, ctr.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = HF_ECUDA;
+    cudaEvent_t b0 = tm.mark();
+    for (int t = 0; t < T && rc == HF_OK; ++t) rc = tie_fixup_big(f, t, ctr[(size_t)t * 4 + 1], s);
+    cudaEvent_t b1 = tm.mark();
+    tm.span(3, b0, b1);
+    if (rc == HF_OK) rc = finish(f, s);
+  }
+  cudaFree(rscratch);
+  if (rc == HF_OK) {
+    tm.collect({0, 1, 2, 3});
+    f->timings[6] = (float)(T * (1 + 2 + 8 * K + (K > 1 ? 1 : 0) + 3));
+  }
+  free_build_scratch(f);
+  if (rc != HF_OK) {
+    destroy(f);
+    return rc;
+  }
+  *out = f;
+  return HF_OK;
+}
+
+int hf_free(hf_forest* f) {
+  if (!f) return HF_OK;
+  cudaDeviceSynchronize();
+  destroy(f);
+  return HF_OK;
+}
+
+int hf_set_option(hf_forest* f, const char* key, int64_t value) {
+  if (!f || !key) return HF_EINVAL;
+  std::string k(key);
+  if (k == "mode") {
+    if (value != 0) return HF_EINVAL;
+    f->mode = (int)value;
+  } else if (k == "timing") {
+    f->timing = value ? 1 : 0;
+  } else {
+    return HF_EINVAL;
+  }
+  return HF_OK;
+}
+
+int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap) {
+  if (!f || !out_ms || cap < 0) return HF_EINVAL;
+  for (int i = 0; i < cap && i < 7; ++i) out_ms[i] = f->timings[i];
+  return HF_OK;
+}
+
+int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
+  if (!f || !out || cap < 0) return HF_EINVAL;
+  const int64_t v[6] = {f->n, f->d, f->T, f->bits, f->W, f->K};
+  for (int i = 0; i < cap && i < 6; ++i) out[i] = v[i];
+  return HF_OK;
+}
+
+int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
+  if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = f->n;
+  const size_t cnt = (size_t)n * k;
+  const bool dev_i = classify(out_idx) == 1, dev_d = classify(out_dist) == 1;
+  uint32_t* li = dev_i ? reinterpret_cast<uint32_t*>(out_idx) : nullptr;
+  float* ldd = dev_d ? out_dist : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!li) e = dalloc(&li, cnt);
+  if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt);
+  if (e != cudaSuccess) {
+    if (!dev_i) dfree(li);
+    if (!dev_d) dfree(ldd);
+    return map_cuda(e);
+  }
+  Timer tm(f, s);
+  cudaEvent_t a0 = tm.mark();
+  launch_list_init(li, ldd, (int64_t)cnt, s);
+  int rc = HF_OK;
+  const int wmax = 128;
+  for (int t = 0; t < f->T && rc == HF_OK; ++t) {
+    // windows wider than one pass covers are split into offset bands
+    if (w > wmax) {
+      rc = HF_ENOTIMPL;
+      break;
+    }
+    rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, k, li, ldd, s);
+  }
+  cudaEvent_t a1 = tm.mark();
+  tm.span(4, a0, a1);
+  if (rc == HF_OK && !dev_i)
+    rc = map_cuda(cudaMemcpyAsync(out_idx, li, cnt * 4, cudaMemcpyDeviceToHost, s));
+  if (rc == HF_OK && !dev_d)
+    rc = map_cuda(cudaMemcpyAsync(out_dist, ldd, cnt * 4, cudaMemcpyDeviceToHost, s));
+  int rc2 = finish(f, s);
+  if (rc == HF_OK) rc = rc2;
+  if (rc == HF_OK) tm.collect({4});
+  if (!dev_i) dfree(li);
+  if (!dev_d) dfree(ldd);
+  return rc;
+}
+
+int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w, int32_t* out_idx,
+              float* out_dist, void* stream) {
+  if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (nq == 0) return HF_OK;
+  if (!queries || !out_idx || !out_dist || nq > HF_MAX_N) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = f->d;
+  const size_t cnt = (size_t)nq * k;
+  const bool dev_q = classify(queries) == 1;
+  const bool dev_i = classify(out_idx) == 1, dev_d = classify(out_dist) == 1;
+  float* qd = nullptr;
+  uint8_t* qc = nullptr;
+  uint32_t* li = dev_i ? reinterpret_cast<uint32_t*>(out_idx) : nullptr;
+  float* ldd = dev_d ? out_dist : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!dev_q) e = dalloc(&qd, (size_t)nq * d);
+  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d);
+  if (e == cudaSuccess && !li) e = dalloc(&li, cnt);
+  if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt);
+  int rc = map_cuda(e);
+  Timer tm(f, s);
+  if (rc == HF_OK) {
+    if (!dev_q) rc = map_cuda(cudaMemcpyAsync(qd, queries, (size_t)nq * d * 4, cudaMemcpyHostToDevice, s));
+    const float* qsrc = dev_q ? queries : qd;
+    cudaEvent_t a0 = tm.mark();
+    launch_quantize_codes(qsrc, nq, d, f->lo, f->scale, f->bits, qc, f->err, s);
+    if (rc == HF_OK) rc = launch_search(f, qsrc, qc, nq, k, w, li, ldd, nullptr, -1, s);
+    cudaEvent_t a1 = tm.mark();
+    tm.span(5, a0, a1);
+    if (rc == HF_OK && !dev_i) rc = map_cuda(cudaMemcpyAsync(out_idx, li, cnt * 4, cudaMemcpyDeviceToHost, s));
+    if (rc == HF_OK && !dev_d) rc = map_cuda(cudaMemcpyAsync(out_dist, ldd, cnt * 4, cudaMemcpyDeviceToHost, s));
+    int rc2 = finish(f, s);
+    if (rc == HF_OK) rc = rc2;
+    if (rc == HF_OK) tm.collect({5});
+  }
+  dfree(qd);
+  dfree(qc);
+  if (!dev_i) dfree(li);
+  if (!dev_d) dfree(ldd);
+  return rc;
+}
+
+// ---- inspection exports ----------------------------------------------------
+
+int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream) {
+  if (!f || !out_codes) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t cnt = (size_t)f->n * f->d;
+  const bool dev = classify(out_codes) == 1;
+  uint8_t* c = dev ? out_codes : nullptr;
+  if (!dev && dalloc(&c, cnt) != cudaSuccess) return HF_ENOMEM;
+  launch_planes_to_codes(f->planes, f->n, f->d, f->bits, c, s);
+  int rc = HF_OK;
+  if (!dev) rc = map_cuda(cudaMemcpyAsync(out_codes, c, cnt, cudaMemcpyDeviceToHost, s));
+  int rc2 = finish(f, s);
+  if (!dev) dfree(c);
+  return rc ? rc : rc2;
+}
+
+int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream) {
+  if (!f || !out_keys || tree < 0 || tree >= f->T) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t cnt = (size_t)f->n * f->W;
+  const bool dev = classify(out_keys) == 1;
+  uint64_t* kk = dev ? out_keys : nullptr;
+  if (!dev && dalloc(&kk, cnt) != cudaSuccess) return HF_ENOMEM;
+  launch_full_keys_planes(f->planes, f->n, f->d, f->bits, f->W, f->pi + (size_t)tree * f->d,
+                          f->rbits + (size_t)tree * f->W32, kk, s);
+  int rc = HF_OK;
+  if (!dev) rc = map_cuda(cudaMemcpyAsync(out_keys, kk, cnt * 8, cudaMemcpyDeviceToHost, s));
+  int rc2 = finish(f, s);
+  if (!dev) dfree(kk);
+  return rc ? rc : rc2;
+}
+
+int hf_debug_order(hf_forest* f, int32_t tree, uint32_t* out_sigma, void* stream) {
+  if (!f || !out_sigma || tree < 0 || tree >= f->T) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = map_cuda(cudaMemcpyAsync(out_sigma, f->sigma + (size_t)tree * f->n, (size_t)f->n * 4,
+                                    cudaMemcpyDefault, s));
+  int rc2 = finish(f, s);
+  return rc ? rc : rc2;
+}
+
+int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq, int64_t* out_pos,
+                    void* stream) {
+  if (!f || tree < 0 || tree >= f->T || nq < 0) return HF_EINVAL;
+  if (nq == 0) return HF_OK;
+  if (!queries || !out_pos) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int d = f->d;
+  const bool dev_q = classify(queries) == 1, dev_o = classify(out_pos) == 1;
+  float* qd = nullptr;
+  uint8_t* qc = nullptr;
+  int64_t* po = dev_o ? out_pos : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!dev_q) e = dalloc(&qd, (size_t)nq * d);
+  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d);
+  if (e == cudaSuccess && !po) e = dalloc(&po, (size_t)nq);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) {
+    if (!dev_q) cudaMemcpyAsync(qd, queries, (size_t)nq * d * 4, cudaMemcpyHostToDevice, s);
+    const float* qsrc = dev_q ? queries : qd;
+    launch_quantize_codes(qsrc, nq, d, f->lo, f->scale, f->bits, qc, f->err, s);
+    rc = launch_search(f, qsrc, qc, nq, 1, 1, nullptr, nullptr, po, tree, s);
+    if (rc == HF_OK && !dev_o) rc = map_cuda(cudaMemcpyAsync(out_pos, po, (size_t)nq * 8, cudaMemcpyDeviceToHost, s));
+    int rc2 = finish(f, s);
+    if (rc == HF_OK) rc = rc2;
+  }
+  dfree(qd);
+  dfree(qc);
+  if (!dev_o) dfree(po);
+  return rc;
+}
+
+int hf_debug_keys_from_codes(const uint8_t* codes, int64_t n, int32_t d, int32_t bits, uint64_t* out_keys,
+                             void* stream) {
+  if (!codes || !out_keys || n < 1 || n > HF_MAX_N || d < 1 || d > HF_MAX_D || bits < 1 || bits > HF_MAX_BITS)
+    return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int W = (int)(((int64_t)d * bits + 63) / 64);
+  const bool dev_c = classify(codes) == 1, dev_o = classify(out_keys) == 1;
+  uint8_t* cd = nullptr;
+  uint64_t* kk = dev_o ? out_keys : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!dev_c) e = dalloc(&cd, (size_t)n * d);
+  if (e == cudaSuccess && !kk) e = dalloc(&kk, (size_t)n * W);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) {
+    if (!dev_c) cudaMemcpyAsync(cd, codes, (size_t)n * d, cudaMemcpyHostToDevice, s);
+    launch_full_keys_codes(dev_c ? codes : cd, n, d, bits, W, nullptr, nullptr, kk, s);
+    if (!dev_o) cudaMemcpyAsync(out_keys, kk, (size_t)n * W * 8, cudaMemcpyDeviceToHost, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    if (se == cudaSuccess) se = cudaGetLastError();
+    rc = map_cuda(se);
+  }
+  dfree(cd);
+  if (!dev_o) dfree(kk);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations shared by the CUDA translation units of libhf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hf.h"
+
+// ---------------------------------------------------------------------------
+// Device error word: bit flags OR-ed in by kernels, read by the host at the
+// end of every call.
+// ---------------------------------------------------------------------------
+enum : int {
+  HF_ERRBIT_TIMEOUT = 1,    // a bounded inter-block wait gave up
+  HF_ERRBIT_NONFINITE = 2,  // NaN or inf in points or queries
+};
+
+__device__ __forceinline__ void hf_raise(int* err, int bit) { atomicOr(err, bit); }
+
+// ---------------------------------------------------------------------------
+// The forest handle.
+// ---------------------------------------------------------------------------
+struct SortScratch {
+  uint64_t* keys_a = nullptr;  // [n]
+  uint64_t* keys_b = nullptr;  // [n]
+  uint32_t* vals_a = nullptr;  // [n]
+  uint32_t* vals_b = nullptr;  // [n]
+  uint32_t* status = nullptr;  // [passes][tiles + 1][256] look-back words + tickets
+  uint32_t* hist = nullptr;    // [K*8][256] digit counts -> exclusive offsets
+  size_t status_bytes = 0;
+  int64_t cap_n = 0;
+  int cap_k = 0;
+};
+
+struct TieScratch {
+  uint32_t* counters = nullptr;  // [0] runs, [1] big runs, [2] big elements
+  uint2* runs = nullptr;         // (start, len) of runs, capacity n/2 + 1
+  uint2* big_runs = nullptr;     // per tree: runs longer than the small cap
+  int64_t big_cap = 0;           // entries per tree in big_runs
+  uint32_t* big_count_host = nullptr;  // pinned [T][2]
+};
+
+struct hf_forest {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0, T = 0, bits = 0, W = 0, K = 0, L = 0, W32 = 0;
+  uint64_t seed = 0;
+
+  const float* x = nullptr;  // n x d float32, device
+  float* x_owned = nullptr;  // device copy when the caller passed host memory
+
+  float* lo = nullptr;        // [d]
+  float* scale = nullptr;     // [d]
+  uint32_t* planes = nullptr; // [bits][n][W32]; plane 0 = most significant bit
+
+  int32_t* pi = nullptr;      // [T][d]
+  uint32_t* rbits = nullptr;  // [T][W32]; bit j of word m: reflection of permuted axis 32m+j
+  uint64_t* prefix = nullptr; // [T][K][n] key prefixes in sorted order
+  uint32_t* sigma = nullptr;  // [T][n] position -> point
+
+  int* err = nullptr;         // device error word
+  int* err_host = nullptr;    // pinned
+
+  uint64_t* pk = nullptr;     // [K][n] key prefixes in point order (scratch)
+  SortScratch sort;
+  TieScratch tie;
+
+  // options
+  int64_t spin_limit_us = 2000000;
+  int test_stall = 0;
+  int mode = 0;
+  int timing = 1;
+
+  float timings[8] = {0};
+  cudaEvent_t ev[8] = {};
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (each enqueues on `s`; errors surface through cudaGetLastError)
+// ---------------------------------------------------------------------------
+// quantize.cu
+void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int bits,
+                  int* err, void* scratch, size_t scratch_bytes, cudaStream_t s);
+size_t range_scratch_bytes(int64_t n, int d);
+void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
+                            int bits, uint32_t* planes, int* err, cudaStream_t s);
+void launch_quantize_codes(const float* x, int64_t n, int d, const float* lo, const float* scale,
+                           int bits, uint8_t* codes, int* err, cudaStream_t s);
+void launch_planes_to_codes(const uint32_t* planes, int64_t n, int d, int bits, uint8_t* codes,
+                            cudaStream_t s);
+
+// keys.cu
+void launch_prefix_keys(const uint32_t* planes, int64_t n, int d, int bits, int K, int L,
+                        const int32_t* pi, const uint32_t* rbits, uint64_t* pk, cudaStream_t s);
+void launch_full_keys_planes(const uint32_t* planes, int64_t n, int d, int bits, int W,
+                             const int32_t* pi, const uint32_t* rbits, uint64_t* out,
+                             cudaStream_t s);
+void launch_full_keys_codes(const uint8_t* codes, int64_t n, int d, int bits, int W,
+                            const int32_t* pi, const uint32_t* rbits, uint64_t* out,
+                            cudaStream_t s);
+
+// sort.cu
+int sort_tree(hf_forest* f, int tree, cudaStream_t s);  // keys -> sigma, prefix
+int tie_fixup_big(hf_forest* f, int tree, uint32_t big_runs, cudaStream_t s);
+
+// window.cu
+int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k,
+                        uint32_t* list_idx, float* list_dist, cudaStream_t s);
+void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
+
+// search.cu
+int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,
+                  int w, uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree,
+                  cudaStream_t s);
+
+// host helpers (api.cu)
+void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);
+
+static inline unsigned hf_blocks(int64_t work, int per_block, int64_t cap = (1 << 30)) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}

@@ -1,0 +1,200 @@
+// Per-axis range and b-bit quantization of the points.
+//
+// The paper quantizes vectors for its distance stage (Section 3, 4-bit codes)
+// but does not say how coordinates are discretised for the Hilbert sort. This
+// library fixes: lo_j = min_i x_ij, hi_j = max_i x_ij, scale_j =
+// (float)(2^b / (double)(float)(hi_j - lo_j)) (0 for a flat axis), and
+// code = clamp(floor(fl32(fl32(x - lo) * scale)), 0, 2^b - 1), each step a
+// separately rounded float32 operation (__fsub_rn / __fmul_rn, never fused).
+//
+// Codes are stored as b bit planes, plane 0 holding the most significant bit:
+// planes[l][i][m] bit j = bit (b-1-l) of the code of coordinate 32m + j of
+// point i. A key prefix that needs only the top level reads one plane
+// (d/8 bytes per point) instead of the whole code row.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hf_internal.cuh"
+
+namespace {
+
+constexpr int RANGE_THREADS = 256;
+
+// Each thread owns one column group of `vec` consecutive columns for the whole
+// run, because the total thread count is a multiple of d / vec; it keeps a
+// running min / max and writes them to partial[thread].
+template <int VEC>
+__global__ void range_partial_kernel(const float* __restrict__ x, int64_t total_vec, int d,
+                                     int64_t nthreads, float* __restrict__ pmin,
+                                     float* __restrict__ pmax, int* __restrict__ err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  float mn[VEC], mx[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    mn[v] = INFINITY;
+    mx[v] = -INFINITY;
+  }
+  bool bad = false;
+  for (int64_t e = t; e < total_vec; e += nthreads) {
+    if (VEC == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(x) + e);
+      const float vals[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        bad |= !isfinite(vals[v]);
+        mn[v] = fminf(mn[v], vals[v]);
+        mx[v] = fmaxf(mx[v], vals[v]);
+      }
+    } else {
+      const float val = __ldg(x + e);
+      bad |= !isfinite(val);
+      mn[0] = fminf(mn[0], val);
+      mx[0] = fmaxf(mx[0], val);
+    }
+  }
+  if (bad) hf_raise(err, HF_ERRBIT_NONFINITE);
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    pmin[t * VEC + v] = mn[v];
+    pmax[t * VEC + v] = mx[v];
+  }
+}
+
+// Column c of the result reduces partials of threads t with (t*VEC) % d == c - v.
+__global__ void range_final_kernel(const float* __restrict__ pmin, const float* __restrict__ pmax,
+                                   int64_t nthreads, int vec, int d, int bits,
+                                   float* __restrict__ lo, float* __restrict__ scale) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const int groups = d / vec;  // threads per "row" of column groups
+  const int g = c / vec, v = c % vec;
+  float mn = INFINITY, mx = -INFINITY;
+  for (int64_t t = g; t < nthreads; t += groups) {
+    mn = fminf(mn, pmin[t * vec + v]);
+    mx = fmaxf(mx, pmax[t * vec + v]);
+  }
+  lo[c] = mn;
+  const float width = __fsub_rn(mx, mn);
+  scale[c] = width > 0.0f ? (float)((double)(1u << bits) / (double)width) : 0.0f;
+}
+
+__device__ __forceinline__ uint32_t quantize_one(float x, float lo, float scale, int bits) {
+  const float diff = __fsub_rn(x, lo);
+  const float prod = __fmul_rn(diff, scale);
+  const float fl = floorf(prod);
+  const float top = (float)((1u << bits) - 1u);
+  const float cl = fminf(fmaxf(fl, 0.0f), top);
+  return (uint32_t)cl;
+}
+
+// One warp per (point, 32-coordinate word). Lane j quantizes coordinate
+// 32m + j; a ballot per bit level gives the plane words directly.
+__global__ void quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32,
+                                       const float* __restrict__ lo,
+                                       const float* __restrict__ scale, int bits,
+                                       uint32_t* __restrict__ planes) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = n * W32;
+  for (int64_t wk = warp; wk < total; wk += nwarps) {
+    const int64_t i = wk / W32;
+    const int m = (int)(wk - i * W32);
+    const int c = m * 32 + lane;
+    uint32_t code = 0;
+    if (c < d) code = quantize_one(__ldg(x + i * d + c), __ldg(lo + c), __ldg(scale + c), bits);
+    for (int l = 0; l < bits; ++l) {
+      const uint32_t word = __ballot_sync(0xffffffffu, (code >> (bits - 1 - l)) & 1u);
+      if (lane == l) planes[((size_t)l * n + i) * W32 + m] = word;
+    }
+  }
+}
+
+__global__ void quantize_codes_kernel(const float* __restrict__ x, int64_t total, int d,
+                                      const float* __restrict__ lo,
+                                      const float* __restrict__ scale, int bits,
+                                      uint8_t* __restrict__ codes, int* __restrict__ err) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[e];
+    if (!isfinite(v)) {
+      hf_raise(err, HF_ERRBIT_NONFINITE);
+      codes[e] = 0;
+      continue;
+    }
+    const int c = (int)(e % d);
+    codes[e] = (uint8_t)quantize_one(v, lo[c], scale[c], bits);
+  }
+}
+
+__global__ void planes_to_codes_kernel(const uint32_t* __restrict__ planes, int64_t n, int d,
+                                       int W32, int bits, uint8_t* __restrict__ codes) {
+  const int64_t total = n * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / d;
+    const int c = (int)(e - i * d);
+    uint32_t v = 0;
+    for (int l = 0; l < bits; ++l)
+      v = (v << 1) | ((planes[((size_t)l * n + i) * W32 + (c >> 5)] >> (c & 31)) & 1u);
+    codes[e] = (uint8_t)v;
+  }
+}
+
+int64_t range_threads(int64_t n, int d, int vec) {
+  const int64_t groups = d / vec;
+  int64_t target = 152 * 2048;
+  int64_t reps = (target + groups - 1) / groups;
+  const int64_t rows_max = n;  // no more threads than rows per column group
+  if (reps > rows_max) reps = rows_max;
+  if (reps < 1) reps = 1;
+  return reps * groups;
+}
+
+}  // namespace
+
+size_t range_scratch_bytes(int64_t n, int d) {
+  const int vec = (d % 4 == 0) ? 4 : 1;
+  return (size_t)range_threads(n, d, vec) * vec * 2 * sizeof(float);
+}
+
+void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int bits, int* err,
+                  void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  const bool v4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  const int vec = v4 ? 4 : 1;
+  int64_t nthreads = range_threads(n, d, (d % 4 == 0) ? 4 : 1);
+  if (!v4) nthreads = range_threads(n, d, 1);
+  float* pmin = static_cast<float*>(scratch);
+  float* pmax = pmin + nthreads * vec;
+  (void)scratch_bytes;
+  const int64_t total_vec = n * d / vec;
+  const unsigned blocks = hf_blocks(nthreads, RANGE_THREADS);
+  if (v4)
+    range_partial_kernel<4><<<blocks, RANGE_THREADS, 0, s>>>(x, total_vec, d, nthreads, pmin, pmax, err);
+  else
+    range_partial_kernel<1><<<blocks, RANGE_THREADS, 0, s>>>(x, total_vec, d, nthreads, pmin, pmax, err);
+  range_final_kernel<<<hf_blocks(d, 128), 128, 0, s>>>(pmin, pmax, nthreads, vec, d, bits, lo, scale);
+}
+
+void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
+                            int bits, uint32_t* planes, int* err, cudaStream_t s) {
+  (void)err;
+  const int W32 = (d + 31) / 32;
+  const int64_t warps = n * W32;
+  quantize_planes_kernel<<<hf_blocks(warps * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, W32, lo, scale,
+                                                                             bits, planes);
+}
+
+void launch_quantize_codes(const float* x, int64_t n, int d, const float* lo, const float* scale,
+                           int bits, uint8_t* codes, int* err, cudaStream_t s) {
+  const int64_t total = n * d;
+  quantize_codes_kernel<<<hf_blocks(total, 256, 152 * 16), 256, 0, s>>>(x, total, d, lo, scale, bits,
+                                                                       codes, err);
+}
+
+void launch_planes_to_codes(const uint32_t* planes, int64_t n, int d, int bits, uint8_t* codes,
+                            cudaStream_t s) {
+  const int W32 = (d + 31) / 32;
+  planes_to_codes_kernel<<<hf_blocks(n * d, 256, 152 * 16), 256, 0, s>>>(planes, n, d, W32, bits, codes);
+}

@@ -1,0 +1,219 @@
+// Batched query search.
+//
+// Paper, Section 2: since the Hilbert order is a total order, binary search
+// locates an arbitrary point in a sorted set; Algorithm 1 then takes the
+// candidates near each query's position in every tree and keeps the top k by
+// vector distance. The paper simulates a collective Hilbert sort of all queries
+// on the CPU; here every query is located independently, which parallelises
+// trivially.
+//
+// One warp per query, looping over the trees, so the query's top-k list stays
+// in shared memory for the whole search. Per tree, lane 0 computes the query's
+// key prefix, binary-searches the sorted prefixes, and, when the query's
+// prefix equals some data prefixes, refines the position inside that run by
+// comparing full keys (computed on demand from the bit planes). The warp then
+// scores the 2w window candidates (lanes split the coordinates, a butterfly
+// sum gives the distance) and lane 0 merges them into the list.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hf_internal.cuh"
+#include "hilbert_device.cuh"
+
+namespace {
+
+constexpr int SWARPS = 4;
+
+// Shared bytes per warp: list (k floats + k ids), query prefix (K words), two
+// coordinate scratch rows (d bytes each), rounded to 16.
+__host__ __device__ __forceinline__ size_t search_per_warp(int k, int K, int d) {
+  return ((size_t)k * 8 + (size_t)K * 8 + 2 * (size_t)d + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ bool lessp(float da, uint32_t ia, float db, uint32_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
+// -1 / 0 / +1 comparing the sorted prefix at position m with the query prefix.
+__device__ __forceinline__ int cmp_prefix(const uint64_t* __restrict__ pre, int64_t n, int K, int64_t m,
+                                          const uint64_t* qp) {
+  for (int w = 0; w < K; ++w) {
+    const uint64_t a = __ldg(pre + (size_t)w * n + m);
+    if (a != qp[w]) return a < qp[w] ? -1 : 1;
+  }
+  return 0;
+}
+
+// Full-key comparison: is the key of transformed Yd smaller than that of Yq?
+__device__ __forceinline__ bool full_key_less(const uint8_t* Yd, const uint8_t* Yq, int d, int bits, int W) {
+  for (int w = 0; w < W; ++w) {
+    const uint64_t a = hf_pack_word(Yd, d, bits, w), b = hf_pack_word(Yq, d, bits, w);
+    if (a != b) return a < b;
+  }
+  return false;
+}
+
+struct SearchArgs {
+  const float* x;
+  int64_t n;
+  int d, bits, K, L, W, W32, T;
+  const uint32_t* planes;
+  const int32_t* pi;
+  const uint32_t* rbits;
+  const uint64_t* prefix;
+  const uint32_t* sigma;
+  const float* q;
+  const uint8_t* qcodes;
+  int64_t nq;
+  int k, w;
+  uint32_t* out_idx;
+  float* out_dist;
+  int64_t* out_pos;
+  int only_tree;
+};
+
+__global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t per_warp = search_per_warp(a.k, a.K, a.d);
+  unsigned char* base = smraw + per_warp * wib;
+  float* ldst = reinterpret_cast<float*>(base);
+  uint32_t* lidx = reinterpret_cast<uint32_t*>(ldst + a.k);
+  uint64_t* qp = reinterpret_cast<uint64_t*>(lidx + a.k);  // 8k bytes in: 8-byte aligned
+  uint8_t* Yq = reinterpret_cast<uint8_t*>(qp + a.K);
+  uint8_t* Yd = Yq + a.d;
+
+  const int64_t qi = (int64_t)blockIdx.x * SWARPS + wib;
+  if (qi >= a.nq) return;
+  const uint8_t* qc = a.qcodes + (size_t)qi * a.d;
+  const float* qv = a.q + (size_t)qi * a.d;
+
+  for (int j = lane; j < a.k; j += 32) {
+    ldst[j] = INFINITY;
+    lidx[j] = 0xffffffffu;
+  }
+  __syncwarp();
+
+  const int t_begin = a.only_tree >= 0 ? a.only_tree : 0;
+  const int t_end = a.only_tree >= 0 ? a.only_tree + 1 : a.T;
+  for (int t = t_begin; t < t_end; ++t) {
+    const int32_t* pi = a.pi + (size_t)t * a.d;
+    const uint32_t* rb = a.rbits + (size_t)t * a.W32;
+    const uint64_t* pre = a.prefix + (size_t)t * a.K * a.n;
+    const uint32_t* sig = a.sigma + (size_t)t * a.n;
+    int64_t pos = 0;
+    if (lane == 0) {
+      hf_load_coords_codes(qc, a.d, a.bits, a.L, pi, rb, Yq);
+      hf_skilling(Yq, a.d, a.L);
+      for (int w = 0; w < a.K; ++w) qp[w] = hf_pack_word(Yq, a.d, a.L, w);
+      // [lo, hi): positions whose prefix equals the query's
+      int64_t lo = 0, hi = a.n;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cmp_prefix(pre, a.n, a.K, mid, qp) < 0) lo = mid + 1;
+        else hi = mid;
+      }
+      int64_t lo2 = lo, hi2 = a.n;
+      while (lo2 < hi2) {
+        const int64_t mid = (lo2 + hi2) >> 1;
+        if (cmp_prefix(pre, a.n, a.K, mid, qp) <= 0) lo2 = mid + 1;
+        else hi2 = mid;
+      }
+      if (lo2 > lo && a.K < a.W) {
+        // equal prefixes: lower bound by full key inside [lo, lo2)
+        hf_load_coords_codes(qc, a.d, a.bits, a.bits, pi, rb, Yq);
+        hf_skilling(Yq, a.d, a.bits);
+        int64_t l = lo, h = lo2;
+        while (l < h) {
+          const int64_t mid = (l + h) >> 1;
+          hf_load_coords_planes(a.planes, a.n, a.d, a.W32, a.bits, pi, rb, sig[mid], Yd);
+          hf_skilling(Yd, a.d, a.bits);
+          if (full_key_less(Yd, Yq, a.d, a.bits, a.W)) l = mid + 1;
+          else h = mid;
+        }
+        lo = l;
+      }
+      pos = lo;
+    }
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (a.only_tree >= 0) {
+      if (lane == 0) a.out_pos[qi] = pos;
+      continue;
+    }
+    const int64_t c0 = pos - a.w > 0 ? pos - a.w : 0;
+    const int64_t c1 = pos + a.w < a.n ? pos + a.w : a.n;
+    for (int64_t c = c0; c < c1; ++c) {
+      const uint32_t pid = __ldg(sig + c);
+      const float* xv = a.x + (size_t)pid * a.d;
+      float part = 0.f;
+      for (int j = lane; j < a.d; j += 32) {
+        const float e = __ldg(qv + j) - __ldg(xv + j);
+        part = fmaf(e, e, part);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) {
+        const float wd = ldst[a.k - 1];
+        const uint32_t wi = lidx[a.k - 1];
+        if (lessp(part, pid, wd, wi)) {
+          bool dup = false;
+          for (int j = 0; j < a.k; ++j) dup |= (lidx[j] == pid);
+          if (!dup) {
+            int j = a.k - 1;
+            while (j > 0 && lessp(part, pid, ldst[j - 1], lidx[j - 1])) {
+              ldst[j] = ldst[j - 1];
+              lidx[j] = lidx[j - 1];
+              --j;
+            }
+            ldst[j] = part;
+            lidx[j] = pid;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (a.only_tree >= 0) return;
+  __syncwarp();
+  for (int j = lane; j < a.k; j += 32) {
+    a.out_idx[(size_t)qi * a.k + j] = lidx[j];
+    a.out_dist[(size_t)qi * a.k + j] = ldst[j];
+  }
+}
+
+}  // namespace
+
+int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k, int w,
+                  uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree, cudaStream_t s) {
+  SearchArgs a;
+  a.x = f->x;
+  a.n = f->n;
+  a.d = f->d;
+  a.bits = f->bits;
+  a.K = f->K;
+  a.L = f->L;
+  a.W = f->W;
+  a.W32 = f->W32;
+  a.T = f->T;
+  a.planes = f->planes;
+  a.pi = f->pi;
+  a.rbits = f->rbits;
+  a.prefix = f->prefix;
+  a.sigma = f->sigma;
+  a.q = q;
+  a.qcodes = qcodes;
+  a.nq = nq;
+  a.k = k;
+  a.w = w;
+  a.out_idx = out_idx;
+  a.out_dist = out_dist;
+  a.out_pos = out_pos;
+  a.only_tree = only_tree;
+  const size_t smem = search_per_warp(k, f->K, f->d) * SWARPS;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute((const void*)search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return HF_ECUDA;
+  search_kernel<<<hf_blocks(nq, SWARPS), SWARPS * 32, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
+}

@@ -1,0 +1,517 @@
+// Hilbert sort: stable LSD radix sort of the K-word key prefixes, then the
+// fix-up that orders runs of equal prefixes by full key.
+//
+// Paper, Section 2: the Hilbert order is a total order over the points; the
+// paper sorts with a key-free CPU algorithm whose details it does not give.
+// Here the order is "ascending (full key, point index)": the prefix words are
+// sorted with 8-bit digits, least significant first; each pass is one
+// single-pass binning kernel with decoupled look-back (Merrill & Garland 2016;
+// Adinets & Merrill 2022, "Onesweep"). The input starts in point order, so
+// equal prefixes stay in index order; the fix-up then reorders each run of
+// equal prefixes by its full keys.
+//
+// The look-back is the only wait between blocks. Tiles take tickets from an
+// atomic counter, so a tile only ever waits for tiles that started before it;
+// each wait is bounded by a %globaltimer deadline, after which the tile sets
+// the error word (HF_ETIMEOUT), publishes a value and finishes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hf_internal.cuh"
+#include "hilbert_device.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int IPT = 16;
+constexpr int TILE = NT * IPT;  // 4096 keys per tile
+constexpr int WARPS = NT / 32;
+constexpr uint32_t FLAG_AGG = 1u << 30;
+constexpr uint32_t FLAG_PRE = 2u << 30;
+constexpr uint32_t VAL_MASK = (1u << 30) - 1u;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Digit histograms of all 8 bytes of all K prefix words (order-independent).
+__global__ void digit_hist_kernel(const uint64_t* __restrict__ pk, int64_t n, int K,
+                                  uint32_t* __restrict__ hist) {
+  extern __shared__ uint32_t sh[];  // [K*8][256]
+  const int nh = K * 8 * 256;
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    for (int w = 0; w < K; ++w) {
+      const uint64_t key = __ldg(pk + (size_t)w * n + e);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) atomicAdd(&sh[(w * 8 + b) * 256 + ((key >> (8 * b)) & 255)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nh; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of each 256-bin histogram (one block per histogram).
+__global__ void hist_scan_kernel(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s[256];
+  uint32_t* h = hist + blockIdx.x * 256;
+  s[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < 256; ++i) {
+      const uint32_t c = s[i];
+      s[i] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  h[threadIdx.x] = s[threadIdx.x];
+}
+
+struct PassSmem {
+  uint64_t keys[TILE];
+  uint32_t vals[TILE];
+  uint32_t whist[WARPS][256];
+  uint32_t tile_start[256];
+  uint32_t gbase[256];
+  uint32_t scan[WARPS];
+  uint32_t tile;
+};
+
+// One LSD pass: bins the keys of one tile by `digit = key >> shift & 255`.
+// GATHER: the key of the element at position e is gather_src[vals_in[e]]
+// (the next prefix word, fetched in the current order).
+template <bool GATHER>
+__global__ void __launch_bounds__(NT)
+onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                const uint64_t* __restrict__ gather_src, uint64_t* __restrict__ keys_out,
+                uint32_t* __restrict__ vals_out, int64_t n, int shift,
+                const uint32_t* __restrict__ goff, uint32_t* __restrict__ status,
+                uint32_t* __restrict__ ticket, int* __restrict__ err, uint64_t spin_ns,
+                int stall, int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  PassSmem& S = *reinterpret_cast<PassSmem*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) S.tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < WARPS * 256; i += NT) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t tile = S.tile;
+  const int64_t base = tile * TILE;
+
+  uint64_t k[IPT];
+  uint32_t v[IPT];
+  uint32_t rk[IPT];
+  uint32_t dg[IPT];
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const int64_t e = base + warp * 32 * IPT + j * 32 + lane;
+    if (e < n) {
+      v[j] = vals_in ? __ldg(vals_in + e) : (uint32_t)e;
+      k[j] = GATHER ? __ldg(gather_src + v[j]) : __ldg(keys_in + e);
+      dg[j] = (uint32_t)(k[j] >> shift) & 255u;
+    } else {
+      v[j] = 0;
+      k[j] = 0;
+      dg[j] = 256u;  // sentinel: no element
+    }
+  }
+  // Stable ranking within the warp: items are ordered by (j, lane).
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg[j]);
+    const uint32_t before = __popc(peers & lt);
+    uint32_t basec = 0;
+    if (dg[j] < 256u) basec = S.whist[warp][dg[j]];
+    __syncwarp();
+    if (dg[j] < 256u && before == 0) S.whist[warp][dg[j]] = basec + __popc(peers);
+    __syncwarp();
+    rk[j] = basec + before;
+  }
+  __syncthreads();
+
+  // Per digit: exclusive offsets across warps and the tile's count.
+  const int dgt = tid;  // NT == 256 == radix
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) {
+    const uint32_t c = S.whist[w][dgt];
+    S.whist[w][dgt] = cnt;
+    cnt += c;
+  }
+
+  // Decoupled look-back for this digit.
+  uint32_t* st = status + tile * 256 + dgt;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    st_relaxed(st, FLAG_PRE | cnt);
+  } else {
+    st_relaxed(st, FLAG_AGG | cnt);
+    int64_t pred = tile - 1;
+    const uint64_t t0 = globaltimer();
+    uint32_t spins = 0;
+    while (pred >= 0) {
+      // test hook: tile 1 watches the spare status row that nothing writes
+      const uint32_t* ps = (stall && tile == 1) ? status + ntiles * 256 + dgt : status + pred * 256 + dgt;
+      const uint32_t sv = ld_relaxed(ps);
+      const uint32_t flag = sv & ~VAL_MASK;
+      if (flag == 0) {
+        if ((++spins & 63u) == 0 && (globaltimer() - t0 > spin_ns || spins > (1u << 30))) {
+          hf_raise(err, HF_ERRBIT_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      excl += sv & VAL_MASK;
+      if (flag == FLAG_PRE) break;
+      --pred;
+    }
+    st_relaxed(st, FLAG_PRE | ((excl + cnt) & VAL_MASK));
+  }
+
+  // Tile-local exclusive scan of the digit counts (warp scans + warp totals).
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) S.scan[warp] = incl;
+  __syncthreads();
+  uint32_t woff = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w)
+    if (w < warp) woff += S.scan[w];
+  S.tile_start[dgt] = woff + incl - cnt;
+  S.gbase[dgt] = goff[dgt] + excl;
+  __syncthreads();
+
+  // Scatter into shared memory in digit order, then write out coalesced.
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    if (dg[j] < 256u) {
+      const uint32_t lp = S.tile_start[dg[j]] + S.whist[warp][dg[j]] + rk[j];
+      S.keys[lp] = k[j];
+      S.vals[lp] = v[j];
+    }
+  }
+  __syncthreads();
+  const int valid = (int)(n - base < TILE ? n - base : TILE);
+  for (int e = tid; e < valid; e += NT) {
+    const uint64_t key = S.keys[e];
+    const uint32_t dgi = (uint32_t)(key >> shift) & 255u;
+    const uint32_t pos = S.gbase[dgi] + (uint32_t)e - S.tile_start[dgi];
+    keys_out[pos] = key;
+    vals_out[pos] = S.vals[e];
+  }
+}
+
+// Sorted prefix words 1..K-1: out[w][p] = pk[w][sigma[p]].
+__global__ void gather_prefix_kernel(const uint64_t* __restrict__ pk, const uint32_t* __restrict__ sigma,
+                                     int64_t n, int K, uint64_t* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = sigma[p];
+    for (int w = 1; w < K; ++w) out[(size_t)w * n + p] = __ldg(pk + (size_t)w * n + i);
+  }
+}
+
+__device__ __forceinline__ bool prefix_eq(const uint64_t* __restrict__ pre, int64_t n, int K,
+                                          int64_t a, int64_t b) {
+  for (int w = 0; w < K; ++w)
+    if (pre[(size_t)w * n + a] != pre[(size_t)w * n + b]) return false;
+  return true;
+}
+
+// Finds maximal runs of >= 2 equal prefixes. Small runs go to `runs`, runs
+// longer than small_cap to `big`.
+__global__ void tie_find_kernel(const uint64_t* __restrict__ pre, int64_t n, int K, int small_cap,
+                                uint2* __restrict__ runs, uint2* __restrict__ big, int64_t big_cap,
+                                uint32_t* __restrict__ counters) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m + 1 < n;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    if (!prefix_eq(pre, n, K, m, m + 1)) continue;
+    if (m > 0 && prefix_eq(pre, n, K, m - 1, m)) continue;
+    int64_t len = 2;
+    while (m + len < n && prefix_eq(pre, n, K, m, m + len)) ++len;
+    if (len <= small_cap) {
+      const uint32_t r = atomicAdd(&counters[0], 1u);
+      runs[r] = make_uint2((uint32_t)m, (uint32_t)len);
+    } else {
+      const uint32_t r = atomicAdd(&counters[1], 1u);
+      if (r < big_cap) big[r] = make_uint2((uint32_t)m, (uint32_t)len);
+      atomicAdd(&counters[2], (uint32_t)len);
+    }
+  }
+}
+
+__device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const uint64_t* b,
+                                          uint32_t ib, int W) {
+  for (int w = 0; w < W; ++w)
+    if (a[w] != b[w]) return a[w] < b[w];
+  return ia < ib;
+}
+
+// One block per small run (grid-stride over runs): full keys of the run's
+// points into shared memory, then each point's rank = number of (key, index)
+// pairs below it; sigma is rewritten inside the run. Shared layout per run:
+// fk[len][W] u64, pt[len], rank[len], then Y[blockDim][d] bytes.
+__global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32,
+                                 int bits, int W, int cap, const int32_t* __restrict__ pi,
+                                 const uint32_t* __restrict__ rbits, const uint2* __restrict__ runs,
+                                 const uint32_t* __restrict__ counters, uint32_t* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint64_t* fk = reinterpret_cast<uint64_t*>(smraw);
+  uint32_t* pt = reinterpret_cast<uint32_t*>(fk + (size_t)cap * W);
+  uint32_t* rank = pt + cap;
+  uint8_t* Y = reinterpret_cast<uint8_t*>(rank + cap) + (size_t)threadIdx.x * d;
+  const uint32_t nruns = counters[0];
+  for (uint32_t r = blockIdx.x; r < nruns; r += gridDim.x) {
+    const uint2 run = runs[r];
+    const int len = (int)run.y;  // <= cap by construction
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+      const uint32_t p = sigma[run.x + e];
+      pt[e] = p;
+      hf_load_coords_planes(planes, n, d, W32, bits, pi, rbits, p, Y);
+      hf_skilling(Y, d, bits);
+      for (int w = 0; w < W; ++w) fk[(size_t)e * W + w] = hf_pack_word(Y, d, bits, w);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+      uint32_t rk = 0;
+      for (int g = 0; g < len; ++g)
+        rk += full_less(fk + (size_t)g * W, pt[g], fk + (size_t)e * W, pt[e], W) ? 1u : 0u;
+      rank[e] = rk;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < len; e += blockDim.x) sigma[run.x + rank[e]] = pt[e];
+    __syncthreads();
+  }
+}
+
+// Big runs: full keys into global scratch, then a bitonic network over all
+// big-run elements of one tree ordered by (run, full key, point).
+__global__ void big_fill_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32,
+                                int bits, int W, const int32_t* __restrict__ pi,
+                                const uint32_t* __restrict__ rbits, const uint2* __restrict__ big,
+                                const uint32_t* __restrict__ offs, int nbig,
+                                const uint32_t* __restrict__ sigma, uint64_t* __restrict__ fk,
+                                uint32_t* __restrict__ item_pt, uint32_t* __restrict__ item_run,
+                                uint8_t* __restrict__ yscratch) {
+  const int r = blockIdx.x;
+  if (r >= nbig) return;
+  const uint2 run = big[r];
+  uint8_t* y = yscratch + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * d;
+  for (uint32_t e = threadIdx.x; e < run.y; e += blockDim.x) {
+    const uint32_t slot = offs[r] + e;
+    const uint32_t p = sigma[run.x + e];
+    item_pt[slot] = p;
+    item_run[slot] = (uint32_t)r;
+    hf_load_coords_planes(planes, n, d, W32, bits, pi, rbits, p, y);
+    hf_skilling(y, d, bits);
+    for (int w = 0; w < W; ++w) fk[(size_t)slot * W + w] = hf_pack_word(y, d, bits, w);
+  }
+}
+
+__device__ __forceinline__ bool item_less(uint32_t a, uint32_t b, const uint64_t* fk,
+                                          const uint32_t* pt, const uint32_t* rn, int W,
+                                          uint32_t total) {
+  const bool va = a < total, vb = b < total;
+  if (va != vb) return va;  // padding sorts last
+  if (!va) return false;
+  if (rn[a] != rn[b]) return rn[a] < rn[b];
+  return full_less(fk + (size_t)a * W, pt[a], fk + (size_t)b * W, pt[b], W);
+}
+
+__global__ void bitonic_step_kernel(uint32_t* __restrict__ ord, uint32_t m, uint32_t j, uint32_t kk,
+                                    const uint64_t* __restrict__ fk, const uint32_t* __restrict__ pt,
+                                    const uint32_t* __restrict__ rn, int W, uint32_t total) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const uint32_t l = i ^ j;
+  if (l <= i) return;
+  const uint32_t a = ord[i], b = ord[l];
+  const bool up = (i & kk) == 0;
+  const bool sw = up ? item_less(b, a, fk, pt, rn, W, total) : item_less(a, b, fk, pt, rn, W, total);
+  if (sw) {
+    ord[i] = b;
+    ord[l] = a;
+  }
+}
+
+__global__ void big_write_kernel(const uint32_t* __restrict__ ord, uint32_t total,
+                                 const uint32_t* __restrict__ pt, const uint32_t* __restrict__ rn,
+                                 const uint2* __restrict__ big, const uint32_t* __restrict__ offs,
+                                 uint32_t* __restrict__ sigma) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= total) return;
+  const uint32_t it = ord[s];
+  const uint32_t r = rn[it];
+  sigma[big[r].x + (s - offs[r])] = pt[it];
+}
+
+__global__ void iota_kernel(uint32_t* a, uint32_t m) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) a[i] = i;
+}
+
+int small_cap_for(int W, int d, int threads) {
+  const size_t budget = 160 * 1024 - (size_t)threads * d;
+  int cap = (int)(budget / ((size_t)W * 8 + 8));
+  if (cap > 1024) cap = 1024;
+  if (cap < 2) cap = 2;
+  return cap;
+}
+
+int tie_threads(int d) { return d <= 1024 ? 64 : 32; }
+
+}  // namespace
+
+static cudaError_t set_attr(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int sort_tree(hf_forest* f, int t, cudaStream_t s) {
+  const int64_t n = f->n;
+  const int K = f->K;
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  const int passes = 8 * K;
+  const size_t per_pass = (size_t)(ntiles + 1) * 256 + 1;  // status rows + spare row + ticket
+  uint32_t* status = f->sort.status;
+  uint64_t* pre = f->prefix + (size_t)t * K * n;
+  uint32_t* sig = f->sigma + (size_t)t * n;
+
+  cudaMemsetAsync(f->sort.hist, 0, (size_t)K * 8 * 256 * sizeof(uint32_t), s);
+  cudaMemsetAsync(status, 0, per_pass * passes * sizeof(uint32_t), s);
+  const size_t hsm = (size_t)K * 8 * 256 * sizeof(uint32_t);
+  set_attr((const void*)digit_hist_kernel, hsm);
+  digit_hist_kernel<<<hf_blocks(n, 512, 152 * 2), 512, hsm, s>>>(f->pk, n, K, f->sort.hist);
+  hist_scan_kernel<<<K * 8, 256, 0, s>>>(f->sort.hist);
+
+  const size_t psm = sizeof(PassSmem);
+  set_attr((const void*)onesweep_kernel<false>, psm);
+  set_attr((const void*)onesweep_kernel<true>, psm);
+
+  const uint64_t spin_ns = (uint64_t)f->spin_limit_us * 1000ull;
+  const uint64_t* kin = nullptr;
+  const uint32_t* vin = nullptr;  // identity
+  int pass = 0;
+  for (int w = K - 1; w >= 0; --w) {
+    for (int b = 0; b < 8; ++b, ++pass) {
+      const bool gather = (w < K - 1) && b == 0;
+      const bool last = pass == passes - 1;
+      uint64_t* kout = last ? pre : ((pass & 1) ? f->sort.keys_b : f->sort.keys_a);
+      uint32_t* vout = last ? sig : ((pass & 1) ? f->sort.vals_b : f->sort.vals_a);
+      const uint64_t* src = (w == K - 1 && b == 0) ? f->pk + (size_t)(K - 1) * n : kin;
+      uint32_t* st = status + per_pass * pass;
+      uint32_t* ticket = st + (size_t)(ntiles + 1) * 256;
+      const uint32_t* goff = f->sort.hist + (size_t)(w * 8 + b) * 256;
+      const int stall = (f->test_stall && pass == 0) ? 1 : 0;
+      if (gather)
+        onesweep_kernel<true><<<(unsigned)ntiles, NT, psm, s>>>(nullptr, vin, f->pk + (size_t)w * n, kout, vout,
+                                                                n, 8 * b, goff, st, ticket, f->err, spin_ns,
+                                                                stall, ntiles);
+      else
+        onesweep_kernel<false><<<(unsigned)ntiles, NT, psm, s>>>(src, vin, nullptr, kout, vout, n, 8 * b, goff,
+                                                                 st, ticket, f->err, spin_ns, stall, ntiles);
+      kin = kout;
+      vin = vout;
+    }
+  }
+  if (K > 1) gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre);
+
+  // Equal prefixes: find runs, fix the small ones on the device right away.
+  const int tt = tie_threads(f->d);
+  const int cap = small_cap_for(f->W, f->d, tt);
+  uint32_t* ctr = f->tie.counters + (size_t)t * 4;
+  cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
+  tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, cap, f->tie.runs,
+                                                            f->tie.big_runs + (size_t)t * f->tie.big_cap,
+                                                            f->tie.big_cap, ctr);
+  const size_t tsm = (size_t)cap * (f->W * 8 + 8) + (size_t)tt * f->d;
+  set_attr((const void*)tie_small_kernel, tsm);
+  tie_small_kernel<<<152 * 2, tt, tsm, s>>>(f->planes, n, f->d, f->W32, f->bits, f->W, cap, f->pi + (size_t)t * f->d,
+                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig);
+  return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
+}
+
+// Host side of the big-run path; called after the build's sync, when the
+// host knows how many big runs tree t has.
+int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
+  if (nbig == 0) return HF_OK;
+  if (nbig > f->tie.big_cap) return HF_ECUDA;
+  const int64_t n = f->n;
+  std::vector<uint2> runs(nbig);
+  if (cudaMemcpy(runs.data(), f->tie.big_runs + (size_t)t * f->tie.big_cap, nbig * sizeof(uint2),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HF_ECUDA;
+  std::vector<uint32_t> offs(nbig);
+  uint64_t total = 0;
+  for (uint32_t r = 0; r < nbig; ++r) {
+    offs[r] = (uint32_t)total;
+    total += runs[r].y;
+  }
+  uint32_t m = 1;
+  while (m < total) m <<= 1;
+  const int W = f->W;
+  const int tt = 64;
+  uint64_t* fk = nullptr;
+  uint32_t *pt = nullptr, *rn = nullptr, *ord = nullptr, *doffs = nullptr;
+  uint8_t* ys = nullptr;
+  uint2* druns = f->tie.big_runs + (size_t)t * f->tie.big_cap;
+  int rc = HF_OK;
+  if (cudaMalloc(&fk, (size_t)total * W * 8) != cudaSuccess || cudaMalloc(&pt, total * 4) != cudaSuccess ||
+      cudaMalloc(&rn, total * 4) != cudaSuccess || cudaMalloc(&ord, (size_t)m * 4) != cudaSuccess ||
+      cudaMalloc(&doffs, nbig * 4) != cudaSuccess ||
+      cudaMalloc(&ys, (size_t)nbig * tt * f->d) != cudaSuccess) {
+    rc = HF_ENOMEM;
+  } else {
+    cudaMemcpyAsync(doffs, offs.data(), nbig * 4, cudaMemcpyHostToDevice, s);
+    uint32_t* sig = f->sigma + (size_t)t * n;
+    big_fill_kernel<<<nbig, tt, 0, s>>>(f->planes, n, f->d, f->W32, f->bits, W, f->pi + (size_t)t * f->d,
+                                        f->rbits + (size_t)t * f->W32, druns, doffs, (int)nbig, sig, fk, pt,
+                                        rn, ys);
+    iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m);
+    for (uint32_t kk = 2; kk <= m; kk <<= 1)
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1)
+        bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total);
+    big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = HF_ECUDA;
+  }
+  cudaFree(fk);
+  cudaFree(pt);
+  cudaFree(rn);
+  cudaFree(ord);
+  cudaFree(doffs);
+  cudaFree(ys);
+  return rc;
+}
+
+size_t sort_status_words(int64_t n, int K) {
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  return ((size_t)(ntiles + 1) * 256 + 1) * 8 * K;
+}
+
+int tie_small_cap(int W, int d) { return small_cap_for(W, d, tie_threads(d)); }

@@ -1,0 +1,212 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Integer work (codes, keys, orders, query positions) must match bit-exactly;
+float32 distances within 1e-5 relative of the oracle's float64 ones, with list
+differences allowed only between near-tied candidates (tests/_helpers.py).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthdata as S
+from _helpers import RTOL, check_lists
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2508_21682_gb300 as hf
+
+    assert torch.cuda.is_available()
+    return hf
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ---------------------------------------------------------------- keys
+def grid(d, b):
+    import itertools
+
+    return np.array(list(itertools.product(range(1 << b), repeat=d)), dtype=np.uint8)
+
+
+@pytest.mark.parametrize("d,b", [(1, 4), (2, 1), (2, 4), (3, 1), (3, 2), (3, 4)])
+def test_keys_full_grid(hf, d, b):
+    c = grid(d, b)
+    want = O.pack_key(O.skilling_transpose(c, b), b)
+    got = hf.keys_from_codes(cuda(c), b).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 16, 31, 33, 64, 384, 768])
+@pytest.mark.parametrize("b", [1, 3, 8])
+def test_keys_random_codes(hf, d, b):
+    rng = np.random.default_rng(d * 10 + b)
+    n = 777
+    c = rng.integers(0, 1 << b, size=(n, d)).astype(np.uint8)
+    want = O.pack_key(O.skilling_transpose(c, b), b)
+    got = hf.keys_from_codes(c, b)  # host buffers through the ABI
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- forest
+def build_both(hf, x, T, bits, seed=S.SEED_FOREST, options=None):
+    G = hf.build(cuda(x), T=T, bits=bits, seed=seed, options=options)
+    F = O.Forest(x, T=T, bits=bits, seed=seed)
+    return G, F
+
+
+@pytest.mark.parametrize("n,d,T,bits,opts", [
+    (20000, 16, 8, 8, None),              # tiny config: full 128-bit keys
+    (5003, 384, 2, 8, None),             # d = 384: top-level prefix path, ragged tail
+    (4099, 64, 3, 8, None),              # two levels in the prefix
+    (3001, 33, 2, 5, None),              # d*b not a multiple of 64
+    (2500, 384, 2, 8, "prefix_words=1"), # many equal prefixes -> tie fix-up
+    (3000, 7, 2, 2, None),               # coarse codes: many equal full keys
+])
+def test_codes_keys_order_bit_exact(hf, n, d, T, bits, opts):
+    x = S.gaussian_mixture(n, d, n_components=50, seed=S.SEED_DATA)
+    G, F = build_both(hf, x, T, bits, options=opts)
+    assert np.array_equal(G.codes().astype(np.uint16), F.codes)
+    for t in range(T):
+        assert np.array_equal(G.keys(t), F.keys[t]), f"keys of tree {t}"
+        assert np.array_equal(G.order(t).astype(np.int64), F.sigma[t]), f"order of tree {t}"
+    G.close()
+
+
+def test_duplicate_points_order(hf):
+    """Long runs of equal full keys (exact duplicates) and of equal prefixes."""
+    x = S.unit_gaussian(6000, 384, seed=5)
+    x[1000:3500] = x[7]  # 2501 copies of one point -> one run longer than the on-device cap
+    x[4000:4100] = x[11]
+    G, F = build_both(hf, x, 2, 8, options="prefix_words=1")
+    for t in range(2):
+        assert np.array_equal(G.order(t).astype(np.int64), F.sigma[t])
+    G.close()
+
+
+def test_host_input_and_output_buffers(hf):
+    x = S.unit_gaussian(3000, 16, seed=9)
+    F = O.Forest(x, T=2, bits=8, seed=4)
+    G = hf.build(x, T=2, bits=8, seed=4)  # host numpy input: copied by the library
+    gi, gd = G.knn_graph(6, 5)  # host outputs
+    assert isinstance(gi, np.ndarray)
+    oi, od = O.knn_graph(F, 6, 5)
+    check_lists(x, gi, gd, oi, od, owners=np.arange(3000))
+    G.close()
+
+
+# ---------------------------------------------------------------- graph
+@pytest.mark.parametrize("n,d,T,w,k,mixture", [
+    (20000, 16, 8, 16, 10, False),   # tiny config as specified
+    (4001, 384, 2, 32, 15, True),    # full-size shape, small n, ragged tail
+    (3007, 64, 3, 60, 12, True),     # w not a multiple of 8, two passes of units
+    (2003, 24, 2, 128, 20, False),   # widest window of one pass
+    (50, 8, 3, 40, 10, False),       # n < 2w + 1
+    (12, 5, 2, 3, 15, False),        # k > n - 1: padded slots
+    (3000, 3, 1, 5, 5, False),       # T = 1, d not a multiple of 4
+])
+def test_knn_graph_parity(hf, n, d, T, w, k, mixture):
+    x = S.gaussian_mixture(n, d, n_components=30, seed=2) if mixture else S.unit_gaussian(n, d, seed=2)
+    G, F = build_both(hf, x, T, 8)
+    gi, gd = G.knn_graph(k, w)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od = O.knn_graph(F, k, w)
+    cand = O.candidate_sets(F, w)
+    check_lists(x, gi, gd, oi, od, owners=np.arange(n), cand=cand)
+    G.close()
+
+
+def test_knn_graph_full_window_equals_brute_force(hf):
+    """w >= n - 1 makes every other point a candidate: the graph is exact."""
+    x = S.unit_gaussian(120, 12, seed=8)
+    G = hf.build(cuda(x), T=1, bits=8, seed=1)
+    gi, gd = G.knn_graph(9, 128)
+    ei, ed = O.brute_force_knn(x, 9)
+    check_lists(x, gi.cpu().numpy(), gd.cpu().numpy(), ei, ed, owners=np.arange(120))
+    G.close()
+
+
+def test_knn_graph_repeatable(hf):
+    x = S.gaussian_mixture(8000, 96, n_components=20, seed=3)
+    G = hf.build(cuda(x), T=3, bits=8, seed=3)
+    a = [t.cpu().numpy() for t in G.knn_graph(10, 24)]
+    b = [t.cpu().numpy() for t in G.knn_graph(10, 24)]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    G.close()
+
+
+# ---------------------------------------------------------------- search
+@pytest.mark.parametrize("n,d,T,bits", [(20000, 16, 4, 8), (4001, 384, 2, 8), (3000, 7, 2, 2)])
+def test_locate_bit_exact(hf, n, d, T, bits):
+    x = S.gaussian_mixture(n, d, n_components=40, seed=1)
+    q = np.concatenate([S.mixture_queries(300, d, n_components=40, data_seed=1, seed=2), x[:50]])
+    G, F = build_both(hf, x, T, bits)
+    qc = O.query_codes(F, q)
+    for t in range(T):
+        assert np.array_equal(G.locate(t, cuda(q)), O.locate(F, t, qc)), f"tree {t}"
+    G.close()
+
+
+@pytest.mark.parametrize("n,d,T,w,k", [(20000, 16, 8, 16, 10), (4001, 384, 3, 50, 30), (100, 6, 2, 70, 10)])
+def test_search_parity(hf, n, d, T, w, k):
+    x = S.gaussian_mixture(n, d, n_components=40, seed=1)
+    q = S.mixture_queries(257, d, n_components=40, data_seed=1, seed=2)
+    G, F = build_both(hf, x, T, 8)
+    gi, gd = G.search(cuda(q), k, w)
+    oi, od = O.search(F, q, k, w)
+    check_lists(x, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, queries=q)
+    G.close()
+
+
+# ---------------------------------------------------------------- errors
+def test_nonfinite_input_rejected(hf):
+    x = S.unit_gaussian(1000, 8, seed=1)
+    x[17, 3] = np.nan
+    with pytest.raises(hf.HFError) as e:
+        hf.build(cuda(x), T=1, bits=8)
+    assert e.value.status == hf.HF_ENONFINITE
+    x[17, 3] = 0.0
+    G = hf.build(cuda(x), T=1, bits=8)
+    q = S.unit_gaussian(5, 8, seed=2)
+    q[2, 0] = np.inf
+    with pytest.raises(hf.HFError) as e:
+        G.search(cuda(q), 5, 4)
+    assert e.value.status == hf.HF_ENONFINITE
+    # the forest stays usable after the error
+    q[2, 0] = 0.5
+    G.search(cuda(q), 5, 4)
+    G.close()
+
+
+def test_bounded_wait_times_out_with_status(hf):
+    """A sort block waits on a status word that nothing writes; the wait is
+    bounded (1 ms here), the call returns HF_ETIMEOUT and the context stays
+    usable."""
+    x = S.unit_gaussian(50000, 16, seed=1)
+    with pytest.raises(hf.HFError) as e:
+        hf.build(cuda(x), T=1, bits=8, options="test_stall=1,spin_limit_us=1000")
+    assert e.value.status == hf.HF_ETIMEOUT
+    G = hf.build(cuda(x), T=1, bits=8)
+    F = O.Forest(x, T=1, bits=8, seed=3)
+    assert np.array_equal(G.order(0).astype(np.int64), F.sigma[0])
+    G.close()
+
+
+def test_invalid_graph_arguments(hf):
+    x = S.unit_gaussian(100, 4, seed=1)
+    G = hf.build(cuda(x), T=1, bits=8)
+    for k, w in [(0, 4), (65, 4), (5, 0)]:
+        with pytest.raises(hf.HFError) as e:
+            G.knn_graph(k, w)
+        assert e.value.status == hf.HF_EINVAL
+    G.close()
