@@ -94,8 +94,6 @@ void destroy(hf_forest* f) {
   dfree(f->prefix);
   dfree(f->sigma);
   dfree(f->err);
-  for (auto& e : f->ev)
-    if (e) cudaEventDestroy(e);
   delete f;
 }
 
@@ -130,15 +128,19 @@ int parse_options(hf_forest* f, const char* opts) {
   return HF_OK;
 }
 
+// Per-call CUDA-event spans. Every event is created by mark(), owned by the
+// Timer and destroyed exactly once (an event may end one span and start the
+// next).
 struct Timer {
   hf_forest* f;
   cudaStream_t s;
+  std::vector<cudaEvent_t> events;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[8];
   explicit Timer(hf_forest* ff, cudaStream_t ss) : f(ff), s(ss) {}
   cudaEvent_t mark() {
     cudaEvent_t e = nullptr;
-    if (f->timing) {
-      cudaEventCreate(&e);
+    if (f->timing && cudaEventCreate(&e) == cudaSuccess) {
+      events.push_back(e);
       cudaEventRecord(e, s);
     }
     return e;
@@ -158,16 +160,26 @@ struct Timer {
       if (!spans[sl].empty()) f->timings[sl] = tot;
     }
   }
+  Timer(const Timer&) = delete;
+  Timer& operator=(const Timer&) = delete;
   ~Timer() {
-    for (auto& v : spans)
-      for (auto& p : v) {
-        cudaEventDestroy(p.first);
-        cudaEventDestroy(p.second);
-      }
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
   }
 };
 
 }  // namespace
+
+void hf_after_launch(const char* what, cudaStream_t s) {
+  static const int on = [] {
+    const char* v = getenv("HF_DEBUG");
+    return v && *v && *v != '0';
+  }();
+  if (!on) return;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  fprintf(stderr, "[hf] %s: %s\n", what, cudaGetErrorString(e));
+  fflush(stderr);
+}
 
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r) {
   uint64_t state = seed + (uint64_t)(tree + 1) * GOLDEN_GAMMA;
@@ -215,6 +227,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
       bits > HF_MAX_BITS)
     return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   hf_forest* f = new hf_forest();
   f->n = n;
   f->d = d;
@@ -369,6 +382,7 @@ int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
 int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
   if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
   const size_t cnt = (size_t)n * k;
   const bool dev_i = classify(out_idx) == 1, dev_d = classify(out_dist) == 1;
@@ -415,6 +429,7 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
   if (nq == 0) return HF_OK;
   if (!queries || !out_idx || !out_dist || nq > HF_MAX_N) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const int d = f->d;
   const size_t cnt = (size_t)nq * k;
   const bool dev_q = classify(queries) == 1;
@@ -456,6 +471,7 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
 int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream) {
   if (!f || !out_codes) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const size_t cnt = (size_t)f->n * f->d;
   const bool dev = classify(out_codes) == 1;
   uint8_t* c = dev ? out_codes : nullptr;
@@ -471,6 +487,7 @@ int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream) {
 int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream) {
   if (!f || !out_keys || tree < 0 || tree >= f->T) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const size_t cnt = (size_t)f->n * f->W;
   const bool dev = classify(out_keys) == 1;
   uint64_t* kk = dev ? out_keys : nullptr;
@@ -487,6 +504,7 @@ int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream) 
 int hf_debug_order(hf_forest* f, int32_t tree, uint32_t* out_sigma, void* stream) {
   if (!f || !out_sigma || tree < 0 || tree >= f->T) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   int rc = map_cuda(cudaMemcpyAsync(out_sigma, f->sigma + (size_t)tree * f->n, (size_t)f->n * 4,
                                     cudaMemcpyDefault, s));
   int rc2 = finish(f, s);
@@ -499,6 +517,7 @@ int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq
   if (nq == 0) return HF_OK;
   if (!queries || !out_pos) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const int d = f->d;
   const bool dev_q = classify(queries) == 1, dev_o = classify(out_pos) == 1;
   float* qd = nullptr;
@@ -529,6 +548,7 @@ int hf_debug_keys_from_codes(const uint8_t* codes, int64_t n, int32_t d, int32_t
   if (!codes || !out_keys || n < 1 || n > HF_MAX_N || d < 1 || d > HF_MAX_D || bits < 1 || bits > HF_MAX_BITS)
     return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
   const int W = (int)(((int64_t)d * bits + 63) / 64);
   const bool dev_c = classify(codes) == 1, dev_o = classify(out_keys) == 1;
   uint8_t* cd = nullptr;

@@ -29,9 +29,6 @@ struct SortScratch {
   uint32_t* vals_b = nullptr;  // [n]
   uint32_t* status = nullptr;  // [passes][tiles + 1][256] look-back words + tickets
   uint32_t* hist = nullptr;    // [K*8][256] digit counts -> exclusive offsets
-  size_t status_bytes = 0;
-  int64_t cap_n = 0;
-  int cap_k = 0;
 };
 
 struct TieScratch {
@@ -39,7 +36,6 @@ struct TieScratch {
   uint2* runs = nullptr;         // (start, len) of runs, capacity n/2 + 1
   uint2* big_runs = nullptr;     // per tree: runs longer than the small cap
   int64_t big_cap = 0;           // entries per tree in big_runs
-  uint32_t* big_count_host = nullptr;  // pinned [T][2]
 };
 
 struct hf_forest {
@@ -61,7 +57,6 @@ struct hf_forest {
   uint32_t* sigma = nullptr;  // [T][n] position -> point
 
   int* err = nullptr;         // device error word
-  int* err_host = nullptr;    // pinned
 
   uint64_t* pk = nullptr;     // [K][n] key prefixes in point order (scratch)
   SortScratch sort;
@@ -74,7 +69,6 @@ struct hf_forest {
   int timing = 1;
 
   float timings[8] = {0};
-  cudaEvent_t ev[8] = {};
 };
 
 // ---------------------------------------------------------------------------
@@ -117,6 +111,10 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
 
 // host helpers (api.cu)
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);
+
+// With HF_DEBUG=1 in the environment: synchronise `s` after a launch and print
+// the kernel's name and any CUDA error to stderr (a no-op otherwise).
+void hf_after_launch(const char* what, cudaStream_t s);
 
 static inline unsigned hf_blocks(int64_t work, int per_block, int64_t cap = (1 << 30)) {
   int64_t b = (work + per_block - 1) / per_block;

@@ -142,13 +142,13 @@ void launch_prefix_keys(const uint32_t* planes, int64_t n, int d, int bits, int 
     const size_t smem = (size_t)(64 * K + 2 * K + TOP_THREADS * (W32 + 1)) * sizeof(uint32_t);
     set_smem((const void*)prefix_top_kernel, smem);
     prefix_top_kernel<<<hf_blocks(n, TOP_THREADS), TOP_THREADS, smem, s>>>(planes, n, d, W32, K, pi,
-                                                                           rbits, pk);
+                                                                           rbits, pk); hf_after_launch("prefix_top_kernel", s);
     return;
   }
   const int t = threads_for_bytes_per_thread(d);
   const size_t smem = (size_t)t * d;
   set_smem((const void*)prefix_general_kernel, smem);
-  prefix_general_kernel<<<hf_blocks(n, t), t, smem, s>>>(planes, n, d, W32, K, L, pi, rbits, pk);
+  prefix_general_kernel<<<hf_blocks(n, t), t, smem, s>>>(planes, n, d, W32, K, L, pi, rbits, pk); hf_after_launch("prefix_general_kernel", s);
   (void)bits;
 }
 
@@ -159,7 +159,7 @@ void launch_full_keys_planes(const uint32_t* planes, int64_t n, int d, int bits,
   const int t = threads_for_bytes_per_thread(d);
   const size_t smem = (size_t)t * d;
   set_smem((const void*)full_keys_planes_kernel, smem);
-  full_keys_planes_kernel<<<hf_blocks(n, t), t, smem, s>>>(planes, n, d, W32, bits, W, pi, rbits, out);
+  full_keys_planes_kernel<<<hf_blocks(n, t), t, smem, s>>>(planes, n, d, W32, bits, W, pi, rbits, out); hf_after_launch("full_keys_planes_kernel", s);
 }
 
 void launch_full_keys_codes(const uint8_t* codes, int64_t n, int d, int bits, int W,
@@ -168,5 +168,5 @@ void launch_full_keys_codes(const uint8_t* codes, int64_t n, int d, int bits, in
   const int t = threads_for_bytes_per_thread(d);
   const size_t smem = (size_t)t * d;
   set_smem((const void*)full_keys_codes_kernel, smem);
-  full_keys_codes_kernel<<<hf_blocks(n, t), t, smem, s>>>(codes, n, d, bits, W, pi, rbits, out);
+  full_keys_codes_kernel<<<hf_blocks(n, t), t, smem, s>>>(codes, n, d, bits, W, pi, rbits, out); hf_after_launch("full_keys_codes_kernel", s);
 }

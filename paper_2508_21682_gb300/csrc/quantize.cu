@@ -174,7 +174,8 @@ void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int
     range_partial_kernel<4><<<blocks, RANGE_THREADS, 0, s>>>(x, total_vec, d, nthreads, pmin, pmax, err);
   else
     range_partial_kernel<1><<<blocks, RANGE_THREADS, 0, s>>>(x, total_vec, d, nthreads, pmin, pmax, err);
-  range_final_kernel<<<hf_blocks(d, 128), 128, 0, s>>>(pmin, pmax, nthreads, vec, d, bits, lo, scale);
+  hf_after_launch("range_partial_kernel", s);
+  range_final_kernel<<<hf_blocks(d, 128), 128, 0, s>>>(pmin, pmax, nthreads, vec, d, bits, lo, scale); hf_after_launch("range_final_kernel", s);
 }
 
 void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
@@ -183,18 +184,18 @@ void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, c
   const int W32 = (d + 31) / 32;
   const int64_t warps = n * W32;
   quantize_planes_kernel<<<hf_blocks(warps * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, W32, lo, scale,
-                                                                             bits, planes);
+                                                                             bits, planes); hf_after_launch("quantize_planes_kernel", s);
 }
 
 void launch_quantize_codes(const float* x, int64_t n, int d, const float* lo, const float* scale,
                            int bits, uint8_t* codes, int* err, cudaStream_t s) {
   const int64_t total = n * d;
   quantize_codes_kernel<<<hf_blocks(total, 256, 152 * 16), 256, 0, s>>>(x, total, d, lo, scale, bits,
-                                                                       codes, err);
+                                                                       codes, err); hf_after_launch("quantize_codes_kernel", s);
 }
 
 void launch_planes_to_codes(const uint32_t* planes, int64_t n, int d, int bits, uint8_t* codes,
                             cudaStream_t s) {
   const int W32 = (d + 31) / 32;
-  planes_to_codes_kernel<<<hf_blocks(n * d, 256, 152 * 16), 256, 0, s>>>(planes, n, d, W32, bits, codes);
+  planes_to_codes_kernel<<<hf_blocks(n * d, 256, 152 * 16), 256, 0, s>>>(planes, n, d, W32, bits, codes); hf_after_launch("planes_to_codes_kernel", s);
 }

@@ -214,6 +214,6 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
       cudaFuncSetAttribute((const void*)search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
     return HF_ECUDA;
-  search_kernel<<<hf_blocks(nq, SWARPS), SWARPS * 32, smem, s>>>(a);
+  search_kernel<<<hf_blocks(nq, SWARPS), SWARPS * 32, smem, s>>>(a); hf_after_launch("search_kernel", s);
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }

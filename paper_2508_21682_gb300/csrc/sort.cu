@@ -407,8 +407,8 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
   cudaMemsetAsync(status, 0, per_pass * passes * sizeof(uint32_t), s);
   const size_t hsm = (size_t)K * 8 * 256 * sizeof(uint32_t);
   set_attr((const void*)digit_hist_kernel, hsm);
-  digit_hist_kernel<<<hf_blocks(n, 512, 152 * 2), 512, hsm, s>>>(f->pk, n, K, f->sort.hist);
-  hist_scan_kernel<<<K * 8, 256, 0, s>>>(f->sort.hist);
+  digit_hist_kernel<<<hf_blocks(n, 512, 152 * 2), 512, hsm, s>>>(f->pk, n, K, f->sort.hist); hf_after_launch("digit_hist_kernel", s);
+  hist_scan_kernel<<<K * 8, 256, 0, s>>>(f->sort.hist); hf_after_launch("hist_scan_kernel", s);
 
   const size_t psm = sizeof(PassSmem);
   set_attr((const void*)onesweep_kernel<false>, psm);
@@ -436,6 +436,7 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
       else
         onesweep_kernel<false><<<(unsigned)ntiles, NT, psm, s>>>(src, vin, nullptr, kout, vout, n, 8 * b, goff,
                                                                  st, ticket, f->err, spin_ns, stall, ntiles);
+      hf_after_launch("onesweep_kernel", s);
       kin = kout;
       vin = vout;
     }
@@ -449,11 +450,11 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
   cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
   tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, cap, f->tie.runs,
                                                             f->tie.big_runs + (size_t)t * f->tie.big_cap,
-                                                            f->tie.big_cap, ctr);
+                                                            f->tie.big_cap, ctr); hf_after_launch("tie_find_kernel", s);
   const size_t tsm = (size_t)cap * (f->W * 8 + 8) + (size_t)tt * f->d;
   set_attr((const void*)tie_small_kernel, tsm);
   tie_small_kernel<<<152 * 2, tt, tsm, s>>>(f->planes, n, f->d, f->W32, f->bits, f->W, cap, f->pi + (size_t)t * f->d,
-                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig);
+                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig); hf_after_launch("tie_small_kernel", s);
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
 
@@ -492,12 +493,12 @@ int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
     uint32_t* sig = f->sigma + (size_t)t * n;
     big_fill_kernel<<<nbig, tt, 0, s>>>(f->planes, n, f->d, f->W32, f->bits, W, f->pi + (size_t)t * f->d,
                                         f->rbits + (size_t)t * f->W32, druns, doffs, (int)nbig, sig, fk, pt,
-                                        rn, ys);
-    iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m);
+                                        rn, ys); hf_after_launch("big_fill_kernel", s);
+    iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m); hf_after_launch("iota_kernel", s);
     for (uint32_t kk = 2; kk <= m; kk <<= 1)
       for (uint32_t j = kk >> 1; j > 0; j >>= 1)
-        bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total);
-    big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig);
+        bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total); hf_after_launch("bitonic_step_kernel", s);
+    big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig); hf_after_launch("big_write_kernel", s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = HF_ECUDA;
   }
   cudaFree(fk);

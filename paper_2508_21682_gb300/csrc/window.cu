@@ -223,14 +223,14 @@ int launch_upt(const float* x, int64_t n, int d, const uint32_t* sigma, int w, i
   const unsigned blocks = hf_blocks(n, B);
   // 16-byte loads need every row start 16-byte aligned
   const int vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-  window_kernel<UPT><<<blocks, WNT, smem, s>>>(x, n, d, sigma, w, k, B, wr, vec4, li, ldd);
+  window_kernel<UPT><<<blocks, WNT, smem, s>>>(x, n, d, sigma, w, k, B, wr, vec4, li, ldd); hf_after_launch("window_kernel<UPT>", s);
   return HF_OK;
 }
 
 }  // namespace
 
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s) {
-  list_init_kernel<<<hf_blocks(count, 256, 152 * 8), 256, 0, s>>>(idx, dist, count);
+  list_init_kernel<<<hf_blocks(count, 256, 152 * 8), 256, 0, s>>>(idx, dist, count); hf_after_launch("list_init_kernel", s);
 }
 
 // Chooses B so that (B + wr) / 4 * wr / 8 units fill a multiple of the block.
