@@ -129,7 +129,17 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
     const int64_t e = base + warp * 32 * IPT + j * 32 + lane;
     if (e < n) {
       v[j] = vals_in ? __ldg(vals_in + e) : (uint32_t)e;
-      k[j] = GATHER ? __ldg(gather_src + v[j]) : __ldg(keys_in + e);
+      if (GATHER) {
+        // values are point indices < n unless an earlier pass gave up its
+        // look-back (error word set); never read outside the source then
+        if (v[j] >= (uint64_t)n) {
+          hf_raise(err, HF_ERRBIT_TIMEOUT);
+          v[j] = 0;
+        }
+        k[j] = __ldg(gather_src + v[j]);
+      } else {
+        k[j] = __ldg(keys_in + e);
+      }
       dg[j] = (uint32_t)(k[j] >> shift) & 255u;
     } else {
       v[j] = 0;
@@ -230,10 +240,13 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
 
 // Sorted prefix words 1..K-1: out[w][p] = pk[w][sigma[p]].
 __global__ void gather_prefix_kernel(const uint64_t* __restrict__ pk, const uint32_t* __restrict__ sigma,
-                                     int64_t n, int K, uint64_t* __restrict__ out) {
+                                     int64_t n, int K, uint64_t* __restrict__ out,
+                                     const int* __restrict__ err) {
+  if (*(volatile const int*)err) return;  // the order is not valid: skip
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = sigma[p];
+    if (i >= (uint64_t)n) continue;
     for (int w = 1; w < K; ++w) out[(size_t)w * n + p] = __ldg(pk + (size_t)w * n + i);
   }
 }
@@ -281,8 +294,10 @@ __device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const 
 __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32,
                                  int bits, int W, int cap, const int32_t* __restrict__ pi,
                                  const uint32_t* __restrict__ rbits, const uint2* __restrict__ runs,
-                                 const uint32_t* __restrict__ counters, uint32_t* __restrict__ sigma) {
+                                 const uint32_t* __restrict__ counters, uint32_t* __restrict__ sigma,
+                                 const int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  if (*(volatile const int*)err) return;  // the order is not valid: skip
   uint64_t* fk = reinterpret_cast<uint64_t*>(smraw);
   uint32_t* pt = reinterpret_cast<uint32_t*>(fk + (size_t)cap * W);
   uint32_t* rank = pt + cap;
@@ -294,6 +309,7 @@ __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n,
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
       const uint32_t p = sigma[run.x + e];
       pt[e] = p;
+      if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
       hf_load_coords_planes(planes, n, d, W32, bits, pi, rbits, p, Y);
       hf_skilling(Y, d, bits);
       for (int w = 0; w < W; ++w) fk[(size_t)e * W + w] = hf_pack_word(Y, d, bits, w);
@@ -441,7 +457,7 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
       vin = vout;
     }
   }
-  if (K > 1) gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre);
+  if (K > 1) gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre, f->err);
 
   // Equal prefixes: find runs, fix the small ones on the device right away.
   const int tt = tie_threads(f->d);
@@ -454,7 +470,7 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
   const size_t tsm = (size_t)cap * (f->W * 8 + 8) + (size_t)tt * f->d;
   set_attr((const void*)tie_small_kernel, tsm);
   tie_small_kernel<<<152 * 2, tt, tsm, s>>>(f->planes, n, f->d, f->W32, f->bits, f->W, cap, f->pi + (size_t)t * f->d,
-                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig); hf_after_launch("tie_small_kernel", s);
+                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->err); hf_after_launch("tie_small_kernel", s);
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
 

@@ -58,10 +58,11 @@ def check_lists(x, gi, gd, oi, od, owners=None, queries=None, cand=None, rtol=RT
         assert np.all(ok), f"row {r} not ascending by (dist, idx)"
         assert np.all(valid[r][: valid[r].sum()]), f"hole in row {r}"
     # rank-wise distances
-    tv = np.where(valid, true, 0)
-    ov = np.where(valid, od, 0)
-    ts = np.sort(tv, axis=1)
-    assert np.all(np.abs(ts - ov) <= rtol * ov + 1e-30), "picked distances differ from the oracle's top-k"
+    # valid slots form a prefix of each row (checked above); unfilled ones sort last
+    ts = np.sort(np.where(valid, true, np.inf), axis=1)
+    ov = np.where(valid, od, np.inf)
+    both = valid
+    assert np.all(np.abs(ts[both] - ov[both]) <= rtol * ov[both] + 1e-30), "picked distances differ from the oracle's top-k"
     if cand is not None:
         for r in range(m):
             cs = set(cand[r][cand[r] >= 0].tolist())
