@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the Hilbert-forest path on one GB300 (or N replicas).
+
+One step = the whole path on one synthetic batch: hf_build (range, quantize,
+per-tree keys and sort), hf_knn_graph (window distances + top-k merge over all
+trees) and hf_search (a batch of queries located and answered in every tree).
+
+Default workload: the full-size kNN-graph configuration, n = 3,000,000 points,
+d = 384, float32 unit vectors from a 1,000-component anisotropic Gaussian
+mixture with Zipf(1.1) weights, T trees, b = 8, window w, k = 15; plus 10,000
+mixture queries with N(0, 0.05^2) noise. The paper measured on GOOAQ
+(3M x 384); these seeded synthetic inputs stand in for it.
+
+Prints one JSON line (rank 0). `value` = points / s of the device-resident
+step; `e2e` = the same through the C ABI with pinned host buffers (copies in
+the timed region); `roofline` for the window kernel (the dominant one);
+`cpu_baseline` = the CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle itself (the only reference this
+project has: the paper ships no code) on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kNN-graph points/s at recall@k>=0.8; Hilbert-sort Mkeys/s; % HBM/TC roofline"
+
+# Window-kernel DRAM traffic per launch from the ncu capture summarised in
+# profiles/ (bytes per point per launch, and the source it was taken on).
+WINDOW_TRAFFIC = {"bytes_per_point": None, "source_sha": None}
+
+# GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
+# difference distance is FADD + FFMA = 2 issue slots = 3 flops.
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+
+def args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=3_000_000)
+    p.add_argument("--d", type=int, default=384)
+    p.add_argument("--T", type=int, default=32)
+    p.add_argument("--w", type=int, default=32)
+    p.add_argument("--k", type=int, default=15)
+    p.add_argument("--bits", type=int, default=8)
+    p.add_argument("--nq", type=int, default=10_000)
+    p.add_argument("--components", type=int, default=1000)
+    p.add_argument("--recall-sample", type=int, default=2000)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=20000)
+    return p.parse_args()
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, ws, lr
+
+
+def workload_name(a):
+    return (f"kNN graph + search: n={a.n} d={a.d} mixture({a.components}) T={a.T} b={a.bits} "
+            f"w={a.w} k={a.k}; {a.nq} queries")
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(a, rank):
+    import synthdata as S
+    x = S.gaussian_mixture(a.n, a.d, n_components=a.components, seed=S.SEED_DATA + 1000 * rank)
+    q = S.mixture_queries(a.nq, a.d, n_components=a.components, data_seed=S.SEED_DATA + 1000 * rank,
+                          seed=S.SEED_QUERIES)
+    return x, q
+
+
+def exact_knn_gpu(xd, rows_d, k, exclude=None, chunk=512):
+    """Ground truth for the recall figure: float32 inner-product screen on the
+    GPU (torch matmul, TF32 off), keep k + 16, re-score in float64 on the host
+    with exact coordinate differences, order by (distance, index)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    nrm = (xd * xd).sum(1)
+    out = []
+    keep = k + 16
+    for s in range(0, rows_d.shape[0], chunk):
+        q = rows_d[s:s + chunk]
+        g = nrm[None, :] + (q * q).sum(1)[:, None] - 2.0 * (q @ xd.T)
+        if exclude is not None:
+            g[torch.arange(q.shape[0], device=q.device), exclude[s:s + chunk]] = float("inf")
+        cand = torch.topk(g, keep, dim=1, largest=False).indices
+        for r in range(q.shape[0]):
+            c = cand[r]
+            diff = (xd[c].double() - q[r].double()[None, :])
+            dd = (diff * diff).sum(1).cpu().numpy()
+            cc = c.cpu().numpy()
+            o = np.lexsort((cc, dd))[:k]
+            out.append(cc[o])
+    return np.array(out)
+
+
+def recall(found, exact):
+    k = exact.shape[1]
+    return float(np.mean([len(set(a[a >= 0].tolist()) & set(b.tolist())) / k for a, b in zip(found, exact)]))
+
+
+def run_ours(a):
+    import torch
+    import paper_2508_21682_gb300 as hf
+
+    rank, ws, lr = dist_env()
+    torch.cuda.set_device(lr)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lr))
+    import __graft_entry__ as g
+    g.build()
+    dev = torch.device("cuda", lr)
+    x, q = make_inputs(a, rank)
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q).to(dev)
+    n, d, k, w, T = a.n, a.d, a.k, a.w, a.T
+    gi = torch.empty((n, k), dtype=torch.int32, device=dev)
+    gd = torch.empty((n, k), dtype=torch.float32, device=dev)
+    si = torch.empty((a.nq, k), dtype=torch.int32, device=dev)
+    sd = torch.empty((a.nq, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(tim=None):
+        G = hf.build(xd, T=T, bits=a.bits, seed=3)
+        G.knn_graph(k, w, gi, gd)
+        G.search(qd, k, w, si, sd)
+        if tim is not None:
+            tim.append(G.timings())
+        G.close()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    phases = []
+    l0 = hf.launch_count()
+    with ClockSampler(lr) as clk:
+        for e0, e1 in evs:
+            e0.record(stream)
+            step(phases)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    launches = hf.launch_count() - l0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    ms_step = sum(ms) / len(ms)
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    ph = {kk: statistics.mean(p[kk] for p in phases) for kk in phases[0]}
+    window_ms = ph["window_merge"] / T  # per launch (list init included, < 1%)
+    pairs = n * w - w * (w + 1) // 2
+    flops = 3.0 * d * pairs
+    achieved = flops / (window_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 * 1.5 / 1e12
+    traffic = None
+    src = open(os.path.join(ROOT, "paper_2508_21682_gb300", "csrc", "window.cu"), "rb").read()
+    if WINDOW_TRAFFIC["bytes_per_point"] and WINDOW_TRAFFIC["source_sha"] == hashlib.sha256(src).hexdigest()[:16]:
+        traffic = WINDOW_TRAFFIC["bytes_per_point"] * n
+
+    # recall on a seeded sample (outside the timed region)
+    rng = np.random.default_rng(4)
+    rows = np.sort(rng.choice(n, size=min(a.recall_sample, n), replace=False))
+    rows_t = torch.from_numpy(rows).to(dev)
+    ex = exact_knn_gpu(xd, xd[rows_t], k, exclude=rows_t)
+    rec = recall(gi.cpu().numpy()[rows], ex)
+    qs = min(500, a.nq)
+    exq = exact_knn_gpu(xd, qd[:qs], k)
+    rec_q = recall(si[:qs].cpu().numpy(), exq)
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    gih = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    gdh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    sih = torch.empty((a.nq, k), dtype=torch.int32).pin_memory()
+    sdh = torch.empty((a.nq, k), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for i in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G = hf.build(xh, T=T, bits=a.bits, seed=3)
+        G.knn_graph(k, w, gih, gdh)
+        G.search(qh, k, w, sih, sdh)
+        G.close()
+        torch.cuda.synchronize()
+        if i:  # first one is a warm-up
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.mean(e2e_ms) if e2e_ms else float("nan")
+    if dist:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)
+
+    if rank == 0:
+        clocks = clk.summary()
+        hs_ms = ph["keys"] + ph["sort"] + ph["tie_fixup"]
+        line = {
+            "metric": METRIC,
+            "value": ws * n / (ms_step * 1e-3),
+            "unit": "points/s",
+            "n_gpus": ws,
+            "steps": a.steps,
+            "warmup": a.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
+            "config": {"workload": workload_name(a), "n": n, "d": d, "T": T, "bits": a.bits, "w": w, "k": k,
+                       "queries": a.nq, "mode": "plain f32",
+                       "l2": "inputs larger than L2 (points 4.6 GB per step)",
+                       "parallelism": f"replicas x{ws}"},
+            "recall_at_k": rec,
+            "recall_sample": int(len(rows)),
+            "search_recall_at_k": rec_q,
+            "hilbert_sort_mkeys_s": n * T / (hs_ms * 1e-3) / 1e6,
+            "phase_ms": ph,
+            "roofline": {"bound": "alu", "kernel": "window_kernel (A5+A6, plain f32)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz, 3 flops per FADD+FFMA pair"},
+            "e2e": {"value": ws * n / (e2e_step * 1e-3), "unit": "points/s",
+                    "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
+                    "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
+                    "ms_per_step": e2e_step},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def oracle_sample(a, n_s, T_s, seed_offset=0):
+    """Times the CPU oracle on n_s points of the same mixture, T_s trees."""
+    import oracle as O
+    import synthdata as S
+    x = S.gaussian_mixture(n_s, a.d, n_components=a.components, seed=S.SEED_DATA + seed_offset)
+    q = S.mixture_queries(max(1, a.nq * n_s // a.n), a.d, n_components=a.components,
+                          data_seed=S.SEED_DATA + seed_offset, seed=S.SEED_QUERIES)
+    t0 = time.perf_counter()
+    F = O.Forest(x, T=T_s, bits=a.bits, seed=3)
+    O.knn_graph(F, a.k, a.w)
+    O.search(F, q, a.k, a.w)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(a):
+    try:
+        from threadpoolctl import threadpool_limits
+        lim = threadpool_limits(1)
+    except Exception:
+        lim = None
+    n_s, T_s = min(a.cpu_sample, a.n), 2
+    sec = oracle_sample(a, n_s, T_s)
+    if lim is not None:
+        lim.unregister() if hasattr(lim, "unregister") else None
+    # points/s of the full job: the sample's per-point, per-tree cost times T trees
+    val = n_s / (sec * a.T / T_s)
+    return {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"numpy oracle, {n_s} points of the same mixture, {T_s} of {a.T} trees, w={a.w}, k={a.k}, "
+                      f"queries pro rata; {sec:.1f} s; scaled to {a.T} trees"}
+
+
+def run_reference(a):
+    rank, ws, lr = dist_env()
+    if rank != 0:
+        return
+    n_s, T_s = min(10000, a.n), 1
+    for _ in range(a.warmup):
+        oracle_sample(a, n_s // 4, T_s)
+    secs = [oracle_sample(a, n_s, T_s, seed_offset=i) for i in range(a.steps)]
+    sec = statistics.mean(secs)
+    val = n_s / (sec * a.T / T_s)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": val,
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": sec * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
+        "config": {"workload": workload_name(a), "n": a.n, "d": a.d, "T": a.T, "bits": a.bits, "w": a.w,
+                   "k": a.k, "queries": a.nq},
+        "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"numpy oracle per step: {n_s} points, {T_s} of {a.T} trees, queries pro rata; "
+                                   f"scaled to {a.T} trees"},
+        "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    A = args()
+    if A.impl == "reference":
+        run_reference(A)
+    else:
+        run_ours(A)

@@ -166,6 +166,13 @@ int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
 int hf_info(const hf_forest* f, int64_t* out, int32_t cap);
 
 /*
+ * hf_launch_count -- number of CUDA kernels this library has launched in this
+ * process so far (all forests, all threads). A diagnostic counter: read it
+ * before and after a region to count that region's launches.
+ */
+uint64_t hf_launch_count(void);
+
+/*
  * hf_tree_params -- host-only: the axis permutation pi[d] and reflection bits
  * r[d] of tree `tree` for `seed` (conventions above). Host pointers only.
  */

@@ -30,6 +30,7 @@ SYMBOLS = [
     "hf_build", "hf_build_opts", "hf_knn_graph", "hf_search", "hf_free", "hf_status_string",
     "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
     "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
+    "hf_launch_count",
 ]
 
 _lib = None
@@ -67,11 +68,12 @@ def lib() -> ctypes.CDLL:
         "hf_debug_order": [vp, i32, vp, vp],
         "hf_debug_locate": [vp, i32, vp, i64, vp, vp],
         "hf_debug_keys_from_codes": [vp, i64, i32, i32, vp, vp],
+        "hf_launch_count": [],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "hf_status_string" else ctypes.c_int
+        fn.restype = {"hf_status_string": ctypes.c_char_p, "hf_launch_count": ctypes.c_uint64}.get(name, ctypes.c_int)
     _lib = L
     return L
 
@@ -106,6 +108,11 @@ def _stream(*arrays):
             import torch
             return torch.cuda.current_stream(a.device).cuda_stream
     return None
+
+
+def launch_count() -> int:
+    """Kernels launched by libhf.so in this process so far."""
+    return int(lib().hf_launch_count())
 
 
 def tree_params(seed: int, tree: int, d: int):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -169,7 +170,11 @@ struct Timer {
 
 }  // namespace
 
+// Kernels launched by this library in this process (diagnostic counter).
+static std::atomic<uint64_t> g_launches{0};
+
 void hf_after_launch(const char* what, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   static const int on = [] {
     const char* v = getenv("HF_DEBUG");
     return v && *v && *v != '0';
@@ -208,6 +213,8 @@ const char* hf_status_string(int status) {
     default: return "unknown status";
   }
 }
+
+uint64_t hf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int hf_tree_params(uint64_t seed, int32_t tree, int32_t d, int32_t* pi, uint8_t* r) {
   if (!pi || !r || d < 1 || d > HF_MAX_D || tree < 0) return HF_EINVAL;

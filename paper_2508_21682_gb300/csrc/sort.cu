@@ -457,7 +457,10 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
       vin = vout;
     }
   }
-  if (K > 1) gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre, f->err);
+  if (K > 1) {
+    gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre, f->err);
+    hf_after_launch("gather_prefix_kernel", s);
+  }
 
   // Equal prefixes: find runs, fix the small ones on the device right away.
   const int tt = tie_threads(f->d);
@@ -512,8 +515,10 @@ int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
                                         rn, ys); hf_after_launch("big_fill_kernel", s);
     iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m); hf_after_launch("iota_kernel", s);
     for (uint32_t kk = 2; kk <= m; kk <<= 1)
-      for (uint32_t j = kk >> 1; j > 0; j >>= 1)
-        bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total); hf_after_launch("bitonic_step_kernel", s);
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total);
+        hf_after_launch("bitonic_step_kernel", s);
+      }
     big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig); hf_after_launch("big_write_kernel", s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = HF_ECUDA;
   }
