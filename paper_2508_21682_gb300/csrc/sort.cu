@@ -31,6 +31,7 @@ constexpr int WARPS = NT / 32;
 constexpr uint32_t FLAG_AGG = 1u << 30;
 constexpr uint32_t FLAG_PRE = 2u << 30;
 constexpr uint32_t VAL_MASK = (1u << 30) - 1u;
+constexpr int LB = 16;  // predecessor status words read per look-back round
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   uint32_t v;
@@ -172,7 +173,10 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
     cnt += c;
   }
 
-  // Decoupled look-back for this digit.
+  // Decoupled look-back for this digit. LB predecessor status words are read
+  // at once (independent loads, one round trip), then consumed in order:
+  // aggregates are added until an inclusive prefix ends the walk; a word that
+  // is not ready yet is re-read from there on the next round.
   uint32_t* st = status + tile * 256 + dgt;
   uint32_t excl = 0;
   if (tile == 0) {
@@ -182,21 +186,35 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
     int64_t pred = tile - 1;
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
-    while (pred >= 0) {
-      // test hook: tile 1 watches the spare status row that nothing writes
-      const uint32_t* ps = (stall && tile == 1) ? status + ntiles * 256 + dgt : status + pred * 256 + dgt;
-      const uint32_t sv = ld_relaxed(ps);
-      const uint32_t flag = sv & ~VAL_MASK;
-      if (flag == 0) {
-        if ((++spins & 63u) == 0 && (globaltimer() - t0 > spin_ns || spins > (1u << 30))) {
-          hf_raise(err, HF_ERRBIT_TIMEOUT);
+    for (;;) {
+      uint32_t sv[LB];
+#pragma unroll
+      for (int i = 0; i < LB; ++i) {
+        // test hook: tile 1 watches the spare status row that nothing writes
+        const int64_t pt = pred - i;
+        const uint32_t* ps = (stall && tile == 1) ? status + ntiles * 256 + dgt : status + pt * 256 + dgt;
+        sv[i] = pt >= 0 ? ld_relaxed(ps) : FLAG_PRE;  // before tile 0: prefix 0
+      }
+      int used = 0;
+      bool done = false;
+#pragma unroll
+      for (int i = 0; i < LB; ++i) {
+        if (used != i) break;  // stopped at an earlier word
+        const uint32_t flag = sv[i] & ~VAL_MASK;
+        if (flag == 0) break;
+        excl += sv[i] & VAL_MASK;
+        ++used;
+        if (flag == FLAG_PRE) {
+          done = true;
           break;
         }
-        continue;
       }
-      excl += sv & VAL_MASK;
-      if (flag == FLAG_PRE) break;
-      --pred;
+      if (done) break;
+      pred -= used;
+      if (used == 0 && (++spins & 15u) == 0 && (globaltimer() - t0 > spin_ns || spins > (1u << 28))) {
+        hf_raise(err, HF_ERRBIT_TIMEOUT);
+        break;
+      }
     }
     st_relaxed(st, FLAG_PRE | ((excl + cnt) & VAL_MASK));
   }
