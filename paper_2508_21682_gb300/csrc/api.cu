@@ -13,7 +13,8 @@
 #include "hf_internal.cuh"
 
 size_t sort_status_words(int64_t n, int K);
-int tie_small_cap(int W, int d);
+int tie_small_cap(int W, int d, int bits, int K);
+size_t tie_scratch_words(int W, int d, int bits, int K);
 
 namespace {
 
@@ -81,6 +82,7 @@ void free_build_scratch(hf_forest* f) {
   dfree(f->tie.runs);
   dfree(f->tie.big_runs);
   dfree(f->tie.counters);
+  dfree(f->tie.fk);
 }
 
 void destroy(hf_forest* f) {
@@ -286,11 +288,12 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   chk(dalloc(&f->sort.vals_b, n));
   chk(dalloc(&f->sort.status, sort_status_words(n, K)));
   chk(dalloc(&f->sort.hist, (size_t)K * 8 * 256));
-  const int cap = tie_small_cap(f->W, d);
+  const int cap = tie_small_cap(f->W, d, bits, K);
   f->tie.big_cap = n / (cap + 1) + 1;
   chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1)));
   chk(dalloc(&f->tie.big_runs, (size_t)T * f->tie.big_cap));
   chk(dalloc(&f->tie.counters, (size_t)T * 4));
+  chk(dalloc(&f->tie.fk, K < f->W ? tie_scratch_words(f->W, d, bits, K) : 1));
   void* rscratch = nullptr;
   const size_t rbytes = range_scratch_bytes(n, d);
   chk(cudaMalloc(&rscratch, rbytes));
@@ -300,6 +303,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     return map_cuda(e);
   }
   cudaMemsetAsync(f->err, 0, sizeof(int), s);
+  cudaMemsetAsync(f->tie.counters, 0, (size_t)T * 4 * sizeof(uint32_t), s);
 
   // per-tree permutations and reflection masks (host, then one upload)
   std::vector<int32_t> hpi((size_t)T * d);

@@ -36,6 +36,7 @@ struct TieScratch {
   uint2* runs = nullptr;         // (start, len) of runs, capacity n/2 + 1
   uint2* big_runs = nullptr;     // per tree: runs longer than the small cap
   int64_t big_cap = 0;           // entries per tree in big_runs
+  uint64_t* fk = nullptr;        // full-key scratch of the small-run fix-up
 };
 
 struct hf_forest {

@@ -298,6 +298,7 @@ __global__ void tie_find_kernel(const uint64_t* __restrict__ pre, int64_t n, int
   }
 }
 
+
 __device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const uint64_t* b,
                                           uint32_t ib, int W) {
   for (int w = 0; w < W; ++w)
@@ -305,41 +306,79 @@ __device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const 
   return ia < ib;
 }
 
-// One block per small run (grid-stride over runs): full keys of the run's
-// points into shared memory, then each point's rank = number of (key, index)
-// pairs below it; sigma is rewritten inside the run. Shared layout per run:
-// fk[len][W] u64, pt[len], rank[len], then Y[blockDim][d] bytes.
+// One block per small run (grid-stride over runs). The run's prefixes (words
+// 0..K-1) are equal, so the order inside it is decided by the following key
+// words. Words K..K2-1 lie in the top Lf bit levels, and the top Lf levels of
+// a key equal the Lf-bit key of the coordinates' top Lf bits, so they cost a
+// transform with Lf levels only (at d = 384, K2 = 6: Lf = 1, a running XOR).
+// Each point's rank = number of run members below it by (words K..K2-1,
+// index). Only if two members also tie on those words does the block
+// compute full keys (into its own slice of global scratch) and rank by
+// (full key, index). Shared layout: tk[cap][K2-K], pt[cap], rank[cap],
+// Y[blockDim][d] bytes.
 __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32,
-                                 int bits, int W, int cap, const int32_t* __restrict__ pi,
-                                 const uint32_t* __restrict__ rbits, const uint2* __restrict__ runs,
-                                 const uint32_t* __restrict__ counters, uint32_t* __restrict__ sigma,
+                                 int bits, int W, int K, int K2, int Lf, int cap,
+                                 const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
+                                 const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
+                                 uint32_t* __restrict__ sigma, uint64_t* __restrict__ fk_scratch,
                                  const int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_tie;
   if (*(volatile const int*)err) return;  // the order is not valid: skip
-  uint64_t* fk = reinterpret_cast<uint64_t*>(smraw);
-  uint32_t* pt = reinterpret_cast<uint32_t*>(fk + (size_t)cap * W);
+  const int KT = K2 - K;
+  uint64_t* tk = reinterpret_cast<uint64_t*>(smraw);
+  uint32_t* pt = reinterpret_cast<uint32_t*>(tk + (size_t)cap * KT);
   uint32_t* rank = pt + cap;
   uint8_t* Y = reinterpret_cast<uint8_t*>(rank + cap) + (size_t)threadIdx.x * d;
+  uint64_t* fk = fk_scratch + (size_t)blockIdx.x * cap * W;
   const uint32_t nruns = counters[0];
   for (uint32_t r = blockIdx.x; r < nruns; r += gridDim.x) {
     const uint2 run = runs[r];
     const int len = (int)run.y;  // <= cap by construction
+    if (threadIdx.x == 0) s_tie = 0;
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
       const uint32_t p = sigma[run.x + e];
       pt[e] = p;
       if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
-      hf_load_coords_planes(planes, n, d, W32, bits, pi, rbits, p, Y);
-      hf_skilling(Y, d, bits);
-      for (int w = 0; w < W; ++w) fk[(size_t)e * W + w] = hf_pack_word(Y, d, bits, w);
+      hf_load_coords_planes(planes, n, d, W32, Lf, pi, rbits, p, Y);
+      hf_skilling(Y, d, Lf);
+      for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = hf_pack_word(Y, d, Lf, K + w);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
       uint32_t rk = 0;
-      for (int g = 0; g < len; ++g)
-        rk += full_less(fk + (size_t)g * W, pt[g], fk + (size_t)e * W, pt[e], W) ? 1u : 0u;
+      bool tie = false;
+      for (int g = 0; g < len; ++g) {
+        int c = 0;
+        for (int w = 0; w < KT && c == 0; ++w) {
+          const uint64_t a = tk[(size_t)g * KT + w], b = tk[(size_t)e * KT + w];
+          c = a < b ? -1 : (a > b ? 1 : 0);
+        }
+        if (c == 0 && g != e) tie = true;
+        rk += (c < 0 || (c == 0 && pt[g] < pt[e])) ? 1u : 0u;
+      }
       rank[e] = rk;
+      if (tie) s_tie = 1;
     }
     __syncthreads();
+    if (s_tie && K2 < W) {
+      // rare: the next words tie as well, rank by full keys
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const uint32_t p = pt[e];
+        if (p >= (uint64_t)n) continue;
+        hf_load_coords_planes(planes, n, d, W32, bits, pi, rbits, p, Y);
+        hf_skilling(Y, d, bits);
+        for (int w = 0; w < W; ++w) fk[(size_t)e * W + w] = hf_pack_word(Y, d, bits, w);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        uint32_t rk = 0;
+        for (int g = 0; g < len; ++g)
+          rk += full_less(fk + (size_t)g * W, pt[g], fk + (size_t)e * W, pt[e], W) ? 1u : 0u;
+        rank[e] = rk;
+      }
+      __syncthreads();
+    }
     for (int e = threadIdx.x; e < len; e += blockDim.x) sigma[run.x + rank[e]] = pt[e];
     __syncthreads();
   }
@@ -411,15 +450,30 @@ __global__ void iota_kernel(uint32_t* a, uint32_t m) {
   if (i < m) a[i] = i;
 }
 
-int small_cap_for(int W, int d, int threads) {
-  const size_t budget = 160 * 1024 - (size_t)threads * d;
-  int cap = (int)(budget / ((size_t)W * 8 + 8));
-  if (cap > 1024) cap = 1024;
-  if (cap < 2) cap = 2;
-  return cap;
-}
+constexpr int TIE_THREADS = 64;
+constexpr int TIE_BLOCKS = 152 * 2;
 
-int tie_threads(int d) { return d <= 1024 ? 64 : 32; }
+struct TieGeom {
+  int K2, Lf, cap;
+  size_t smem;
+};
+
+// Words K..K2-1 (up to four) break ties; they lie in the top Lf levels.
+TieGeom tie_geom(int W, int d, int bits, int K) {
+  TieGeom g;
+  g.K2 = K + 4 < W ? K + 4 : W;
+  const int64_t lf = ((int64_t)64 * g.K2 + d - 1) / d;
+  g.Lf = (int)(lf < bits ? lf : bits);
+  const int KT = g.K2 - K;
+  const size_t y = (size_t)TIE_THREADS * d;
+  const size_t per = (size_t)KT * 8 + 8;
+  size_t cap = (96 * 1024 - (y < 96 * 1024 ? y : 96 * 1024)) / per;
+  if (cap > 256) cap = 256;
+  if (cap < 2) cap = 2;
+  g.cap = (int)cap;
+  g.smem = (size_t)g.cap * per + y;
+  return g;
+}
 
 }  // namespace
 
@@ -481,17 +535,22 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
   }
 
   // Equal prefixes: find runs, fix the small ones on the device right away.
-  const int tt = tie_threads(f->d);
-  const int cap = small_cap_for(f->W, f->d, tt);
-  uint32_t* ctr = f->tie.counters + (size_t)t * 4;
-  cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
-  tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, cap, f->tie.runs,
-                                                            f->tie.big_runs + (size_t)t * f->tie.big_cap,
-                                                            f->tie.big_cap, ctr); hf_after_launch("tie_find_kernel", s);
-  const size_t tsm = (size_t)cap * (f->W * 8 + 8) + (size_t)tt * f->d;
-  set_attr((const void*)tie_small_kernel, tsm);
-  tie_small_kernel<<<152 * 2, tt, tsm, s>>>(f->planes, n, f->d, f->W32, f->bits, f->W, cap, f->pi + (size_t)t * f->d,
-                                            f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->err); hf_after_launch("tie_small_kernel", s);
+  // With K == W the prefix is the whole key: equal prefixes are equal keys,
+  // already in index order.
+  if (K < f->W) {
+    const TieGeom tg = tie_geom(f->W, f->d, f->bits, K);
+    uint32_t* ctr = f->tie.counters + (size_t)t * 4;
+    cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
+    tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, tg.cap, f->tie.runs,
+                                                              f->tie.big_runs + (size_t)t * f->tie.big_cap,
+                                                              f->tie.big_cap, ctr);
+    hf_after_launch("tie_find_kernel", s);
+    set_attr((const void*)tie_small_kernel, tg.smem);
+    tie_small_kernel<<<TIE_BLOCKS, TIE_THREADS, tg.smem, s>>>(
+        f->planes, n, f->d, f->W32, f->bits, f->W, K, tg.K2, tg.Lf, tg.cap, f->pi + (size_t)t * f->d,
+        f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->tie.fk, f->err);
+    hf_after_launch("tie_small_kernel", s);
+  }
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
 
@@ -549,9 +608,14 @@ int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
   return rc;
 }
 
+size_t tie_scratch_words(int W, int d, int bits, int K) {
+  const TieGeom g = tie_geom(W, d, bits, K);
+  return (size_t)TIE_BLOCKS * g.cap * W;
+}
+
 size_t sort_status_words(int64_t n, int K) {
   const int64_t ntiles = (n + TILE - 1) / TILE;
   return ((size_t)(ntiles + 1) * 256 + 1) * 8 * K;
 }
 
-int tie_small_cap(int W, int d) { return small_cap_for(W, d, tie_threads(d)); }
+int tie_small_cap(int W, int d, int bits, int K) { return tie_geom(W, d, bits, K).cap; }
