@@ -141,6 +141,33 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
 int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
               int32_t* out_idx, float* out_dist, void* stream);
 
+/*
+ * hf_search_static -- hf_search without any device allocation, for callers
+ * that may not allocate device memory while they run (a serving process with
+ * a memory budget fixed up front, a runtime whose pool owns all device
+ * memory, a latency path that must not take the allocator's locks). The paper
+ * has no counterpart: this is an interface variant of hf_search with the same
+ * results.
+ *
+ * The queries' quantized codes go to a fixed scratch array inside the
+ * library's device image (HF_STATIC_QUERY_BYTES, held by every GPU that loads
+ * the library until the process exits) instead of a per-call allocation.
+ * Limits and rules:
+ *   - nq * d must not exceed HF_STATIC_QUERY_BYTES, else HF_EINVAL;
+ *   - queries, out_idx and out_dist must be device memory (host buffers would
+ *     need staging copies), else HF_EINVAL;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call uses the same array, overwriting it completely: calls that
+ *     overlap on the GPU (other streams, other threads, other forests on the
+ *     same device) race on it and must be serialised by the caller.
+ * Results, status codes and synchronisation are those of hf_search.
+ */
+#define HF_STATIC_QUERY_BYTES (4u << 20)
+int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
+                     int32_t* out_idx, float* out_dist, void* stream);
+
 /* hf_free -- releases the forest and everything it owns (NULL is a no-op). */
 int hf_free(hf_forest* f);
 

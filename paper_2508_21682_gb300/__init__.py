@@ -30,7 +30,7 @@ SYMBOLS = [
     "hf_build", "hf_build_opts", "hf_knn_graph", "hf_search", "hf_free", "hf_status_string",
     "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
     "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
-    "hf_launch_count",
+    "hf_launch_count", "hf_search_static",
 ]
 
 _lib = None
@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
         "hf_debug_locate": [vp, i32, vp, i64, vp, vp],
         "hf_debug_keys_from_codes": [vp, i64, i32, i32, vp, vp],
         "hf_launch_count": [],
+        "hf_search_static": [vp, vp, i64, i32, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -205,6 +206,21 @@ class Forest:
         dp, _b = _ptr(out_dist)
         _check(lib().hf_search(self._h, qp, nq, k, w, ip, dp, _stream(queries, out_idx, out_dist)),
                "hf_search")
+        return out_idx, out_dist
+
+    def search_static(self, queries, k: int, w: int, out_idx=None, out_dist=None):
+        """hf_search_static: same results as search(), no device allocation;
+        queries and outputs must be CUDA tensors."""
+        nq = queries.shape[0]
+        if out_idx is None:
+            out_idx = _empty_like_input(queries, (nq, k), "int32")
+        if out_dist is None:
+            out_dist = _empty_like_input(queries, (nq, k), "float32")
+        qp, _q = _ptr(queries)
+        ip, _a = _ptr(out_idx)
+        dp, _b = _ptr(out_dist)
+        _check(lib().hf_search_static(self._h, qp, nq, k, w, ip, dp, _stream(queries, out_idx, out_dist)),
+               "hf_search_static")
         return out_idx, out_dist
 
     def set_option(self, key: str, value: int):

@@ -217,3 +217,88 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
   search_kernel<<<hf_blocks(nq, SWARPS), SWARPS * 32, smem, s>>>(a); hf_after_launch("search_kernel", s);
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free search.
+//
+// hf_search allocates a device buffer for the queries' quantized codes on
+// every call. Some callers cannot allocate device memory while they run: a
+// serving process that holds a fixed memory budget carved out up front, a
+// host runtime that owns all device memory through its own pool, or a worker
+// that must not take the allocator's locks on its latency path. For them,
+// hf_search_static keeps that scratch in a fixed array that lives in this
+// library's device image: every GPU that loads the library holds
+// HF_STATIC_QUERY_BYTES of it until the process exits.
+//
+// The array's host-side name is only a stand-in for the device symbol, so the
+// host looks up its device address with cudaGetSymbolAddress, once per
+// device, with that device current, and passes that address to the kernels.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+__device__ __align__(256) uint8_t g_static_qcodes[HF_STATIC_QUERY_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint8_t* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_qcodes on the current device (looked up on the
+// first call per device).
+int static_qcodes_address(uint8_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return HF_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_qcodes) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HF_ECUDA;
+    }
+    g_static_addr[dev] = static_cast<uint8_t*>(p);
+  }
+  *out = g_static_addr[dev];
+  return HF_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
+                                int32_t* out_idx, float* out_dist, void* stream) {
+  if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (nq == 0) return HF_OK;
+  if (!queries || !out_idx || !out_dist) return HF_EINVAL;
+  if ((uint64_t)nq * (uint64_t)f->d > (uint64_t)HF_STATIC_QUERY_BYTES) return HF_EINVAL;
+  if (!on_device(queries) || !on_device(out_idx) || !on_device(out_dist)) return HF_EINVAL;
+  uint8_t* qc = nullptr;
+  int rc = static_qcodes_address(&qc);
+  if (rc != HF_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
+  launch_quantize_codes(queries, nq, f->d, f->lo, f->scale, f->bits, qc, f->err, s);
+  rc = launch_search(f, queries, qc, nq, k, w, reinterpret_cast<uint32_t*>(out_idx), out_dist, nullptr, -1, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return HF_ECUDA;
+  if (rc != HF_OK) return rc;
+  int word = 0;
+  if (cudaMemcpy(&word, f->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HF_ECUDA;
+  if (word) {
+    cudaMemset(f->err, 0, sizeof(int));
+    return (word & HF_ERRBIT_NONFINITE) ? HF_ENONFINITE : HF_ETIMEOUT;
+  }
+  return HF_OK;
+}
