@@ -8,17 +8,24 @@
 // of (distance, index), ascending) is merged tree by tree, so the candidate
 // set is never materialised.
 //
-// One block owns B consecutive positions [s, s+B). Every unordered pair of
-// positions (p, q), p < q <= p + w, with at least one end owned by the block
-// is scored once: rows p in [s - wr, s + B) against offsets delta = q - p in
-// [1, wr] (wr = w rounded up to 8; offsets above w are masked). The rows
-// [s - wr, s + B + wr) of the gathered point matrix are staged in shared
-// memory DC coordinates at a time; each thread accumulates a 4-row x 8-offset
-// unit of the band in registers. The band of distances then sits in shared
-// memory, and the thread owning position p merges its right neighbours
-// (p, p + delta) and left neighbours (p - delta, p) into point sigma[p]'s list.
-// Pairs whose two ends belong to different blocks are scored by both blocks
-// (the same arithmetic in the same order, so both see the same value).
+// Work split. A block owns B consecutive positions [s, s+B) and one band of
+// 32 offsets [dlo, dlo+31] (w > 32 takes several launches, one per band).
+// Every pair (p, p + delta), delta in the band, with at least one end owned
+// by the block is scored once per block: rows p in [s - dhi, s + B) (dhi =
+// dlo + 31) against the band's offsets. Each thread owns an 8-row x 8-offset
+// unit of that rectangle and keeps its 64 sums in registers; B + dhi = 512
+// rows make 256 units, one per thread. The rows [s - dhi, s + B + dhi) of the
+// point matrix (gathered through sigma) are staged in shared memory 16
+// coordinates at a time, coordinate-major (xs[c][row]) so that a thread reads
+// 4 consecutive rows of one coordinate with one 16-byte load, by 4-byte
+// cp.async copies double-buffered against the arithmetic. The finished band
+// of distances reuses the staging buffers; then the thread owning position p
+// merges the band's right neighbours (p, p + delta) and left neighbours
+// (p - delta, p) into point sigma[p]'s list, held in registers.
+//
+// Pairs with ends in two blocks are scored by both, with the same arithmetic
+// in the same coordinate order, so both see the same value; (x_p - x_q)^2 and
+// (x_q - x_p)^2 are equal, so a pair scores the same in every tree.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -26,176 +33,194 @@
 
 namespace {
 
-constexpr int WNT = 256;   // threads per block
-constexpr int DC = 32;     // coordinates staged per chunk
-constexpr int XS = DC + 4; // padded row stride of the staged chunk (floats)
-constexpr int UR = 4;      // rows per thread unit
-constexpr int UC = 8;      // offsets per thread unit
-
-struct WinGeom {
-  int B;   // owned positions per block
-  int wr;  // w rounded up to a multiple of UC
-  int NR;  // staged rows = B + 2 wr
-  int units;
-};
+constexpr int WNT = 256;        // threads per block = units per block
+constexpr int DC = 16;          // coordinates per staged chunk
+constexpr int UR = 8;           // rows per unit
+constexpr int UC = 8;           // offsets per unit
+constexpr int WB = 32;          // offsets per band (launch)
+constexpr int ROWS = 512;       // unit rows per block: B + dhi
+constexpr int OG = WB / UC;     // offset groups per band
 
 __device__ __forceinline__ bool lessp(float da, uint32_t ia, float db, uint32_t ib) {
   return da < db || (da == db && ia < ib);
 }
 
-template <int UPT>
-__global__ void __launch_bounds__(WNT)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+  const int sz = valid ? 4 : 0;  // 0: zero-fill, nothing read
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Row pitch of the staging buffers: a multiple of 4 floats (16-byte loads)
+// with an odd number of 16-byte groups, so that rows 8 apart do not share
+// banks.
+__host__ __device__ __forceinline__ int staging_pitch(int NR) {
+  const int p = (NR + 3) & ~3;
+  return ((p >> 2) & 1) ? p : p + 4;
+}
+
+// Stage coordinates [c0, c0 + DC) of staged rows [0, NR) into buf[c][row].
+// Lanes take 16 consecutive coordinates of 2 rows: 64-byte global segments.
+__device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const uint32_t* srow,
+                                            const float* __restrict__ x, int d, int c0) {
+  for (int e = threadIdx.x; e < NR * DC; e += WNT) {
+    const int r = e >> 4, c = e & (DC - 1);
+    const uint32_t pid = srow[r];
+    const bool ok = pid != 0xffffffffu && c0 + c < d;
+    const float* src = ok ? x + (size_t)pid * d + c0 + c : x;
+    cp_async4(buf + c * NRP + r, src, ok);
+  }
+}
+
+// One band of offsets [dlo, dlo + WB - 1] for the block's positions.
+template <int KMAX>
+__global__ void __launch_bounds__(WNT, 2)
 window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sigma, int w,
-              int k, int B, int wr, int vec4, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
+              int k, int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   extern __shared__ __align__(16) float smem[];
-  const int NR = B + 2 * wr;
-  const int nband = B + wr;  // band rows
-  float* xs = smem;                                   // [NR][XS]
-  float* band = xs + (size_t)NR * XS;                 // [nband][wr]
-  uint32_t* srow = reinterpret_cast<uint32_t*>(band + (size_t)nband * wr);  // [NR] point ids
-  float* ld = reinterpret_cast<float*>(srow + NR);    // [k][B]
-  uint32_t* li = reinterpret_cast<uint32_t*>(ld + (size_t)k * B);  // [k][B]
+  const int dhi = dlo + WB - 1;
+  const int NR = B + 2 * dhi;  // staged rows
+  const int NRP = staging_pitch(NR);
+  float* buf0 = smem;
+  float* buf1 = smem + DC * NRP;
+  const int stage_floats = 2 * DC * NRP > ROWS * WB ? 2 * DC * NRP : ROWS * WB;
+  uint32_t* srow = reinterpret_cast<uint32_t*>(smem + stage_floats);
+  float* band = smem;  // [ROWS][WB], after the distance phase
 
   const int64_t s = (int64_t)blockIdx.x * B;
-  const int64_t r0 = s - wr;  // global position of staged row 0
+  const int64_t r0 = s - dhi;  // position of staged row 0
   for (int r = threadIdx.x; r < NR; r += WNT) {
     const int64_t p = r0 + r;
-    srow[r] = (p >= 0 && p < n) ? sigma[p] : 0xffffffffu;
+    srow[r] = (p >= 0 && p < n) ? __ldg(sigma + p) : 0xffffffffu;
   }
-
-  const int ogroups = wr / UC;
-  const int units = (nband / UR) * ogroups;
-  float acc[UPT][UR][UC];
-#pragma unroll
-  for (int u = 0; u < UPT; ++u)
-#pragma unroll
-    for (int a = 0; a < UR; ++a)
-#pragma unroll
-      for (int c = 0; c < UC; ++c) acc[u][a][c] = 0.f;
   __syncthreads();
 
-  for (int c0 = 0; c0 < d; c0 += DC) {
-    const int dc = min(DC, d - c0);
-    // stage rows r0 .. r0 + NR - 1, coordinates c0 .. c0 + dc - 1 (zero padded)
-    if (vec4) {
-      const int per_row = DC / 4;
-      for (int e = threadIdx.x; e < NR * per_row; e += WNT) {
-        const int r = e / per_row, q = e - r * per_row;
-        const uint32_t pid = srow[r];
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pid != 0xffffffffu && 4 * q < dc)
-          v = __ldg(reinterpret_cast<const float4*>(x + (size_t)pid * d + c0) + q);
-        *reinterpret_cast<float4*>(xs + r * XS + 4 * q) = v;
-      }
-    } else {
-      for (int e = threadIdx.x; e < NR * DC; e += WNT) {
-        const int r = e / DC, q = e - r * DC;
-        const uint32_t pid = srow[r];
-        float v = 0.f;
-        if (pid != 0xffffffffu && q < dc) v = __ldg(x + (size_t)pid * d + c0 + q);
-        xs[r * XS + q] = v;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < UPT; ++u) {
-      const int unit = threadIdx.x + u * WNT;
-      if (unit < units) {
-        const int g = unit / ogroups, o = unit - g * ogroups;
-        const int pr = UR * g;            // band row of the unit's first row (= staged row)
-        const int qr = pr + 1 + UC * o;   // staged row of (first row, first offset)
-        for (int j = 0; j < DC; j += 4) {
-          float4 a[UR], b[UR + UC - 1];
-#pragma unroll
-          for (int t = 0; t < UR; ++t) a[t] = *reinterpret_cast<const float4*>(xs + (pr + t) * XS + j);
-#pragma unroll
-          for (int t = 0; t < UR + UC - 1; ++t) b[t] = *reinterpret_cast<const float4*>(xs + (qr + t) * XS + j);
-#pragma unroll
-          for (int t = 0; t < UR; ++t)
-#pragma unroll
-            for (int c = 0; c < UC; ++c) {
-              float e0 = a[t].x - b[t + c].x;
-              float e1 = a[t].y - b[t + c].y;
-              float e2 = a[t].z - b[t + c].z;
-              float e3 = a[t].w - b[t + c].w;
-              float v = acc[u][t][c];
-              v = fmaf(e0, e0, v);
-              v = fmaf(e1, e1, v);
-              v = fmaf(e2, e2, v);
-              v = fmaf(e3, e3, v);
-              acc[u][t][c] = v;
-            }
-        }
-      }
-    }
-    __syncthreads();
-  }
+  // unit of this thread: staged rows pr .. pr+7, offsets dlo + 8o .. dlo + 8o + 7
+  const int g = threadIdx.x / OG, o = threadIdx.x % OG;
+  const int pr = UR * g;
+  const int br = pr + dlo - 1 + UC * o;  // staged row of b[0] (a multiple of 8)
 
-  // band[row][delta-1]: row = staged row of p (p = r0 + row), valid pairs only
+  float acc[UR][UC];
 #pragma unroll
-  for (int u = 0; u < UPT; ++u) {
-    const int unit = threadIdx.x + u * WNT;
-    if (unit < units) {
-      const int g = unit / ogroups, o = unit - g * ogroups;
+  for (int t = 0; t < UR; ++t)
+#pragma unroll
+    for (int c = 0; c < UC; ++c) acc[t][c] = 0.f;
+
+  const int nchunks = (d + DC - 1) / DC;
+  stage_chunk(buf0, NRP, NR, srow, x, d, 0);
+  cp_async_commit();
+  for (int ch = 0; ch < nchunks; ++ch) {
+    float* cur = (ch & 1) ? buf1 : buf0;
+    float* nxt = (ch & 1) ? buf0 : buf1;
+    if (ch + 1 < nchunks) stage_chunk(nxt, NRP, NR, srow, x, d, (ch + 1) * DC);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < DC; ++j) {
+      const float* col = cur + j * NRP;
+      float a[UR], b[16];
+      *reinterpret_cast<float4*>(a) = *reinterpret_cast<const float4*>(col + pr);
+      *reinterpret_cast<float4*>(a + 4) = *reinterpret_cast<const float4*>(col + pr + 4);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(b + 4 * q) = *reinterpret_cast<const float4*>(col + br + 4 * q);
 #pragma unroll
       for (int t = 0; t < UR; ++t)
 #pragma unroll
         for (int c = 0; c < UC; ++c) {
-          const int row = UR * g + t;
-          const int delta = 1 + UC * o + c;
-          const int64_t p = r0 + row, q = p + delta;
-          const bool ok = delta <= w && p >= 0 && q < n && (p >= s || q >= s) && p < s + B;
-          band[row * wr + delta - 1] = ok ? acc[u][t][c] : INFINITY;
+          const float e = a[t] - b[1 + t + c];
+          acc[t][c] = fmaf(e, e, acc[t][c]);
         }
     }
+    __syncthreads();
   }
+  cp_async_wait_0();
   __syncthreads();
 
-  // merge: thread t owns position s + t
-  for (int t = threadIdx.x; t < B; t += WNT) {
-    const int64_t p = s + t;
-    if (p >= n) continue;
-    const int rowp = t + wr;  // staged row of p
+  // band[row][delta - dlo], row = staged row of p (rows < ROWS)
+#pragma unroll
+  for (int t = 0; t < UR; ++t)
+#pragma unroll
+    for (int c = 0; c < UC; ++c) band[(pr + t) * WB + UC * o + c] = acc[t][c];
+  __syncthreads();
+
+  // merge: positions s + tt, tt < B; the point's list is held in registers
+  const int wtop = min(dhi, w);
+  for (int tt = threadIdx.x; tt < B; tt += WNT) {
+    const int64_t p = s + tt;
+    if (p >= n) break;
+    const int rowp = tt + dhi;  // staged row of p
     const uint32_t ip = srow[rowp];
-    for (int j = 0; j < k; ++j) {
-      ld[j * B + t] = ldist[(size_t)ip * k + j];
-      li[j * B + t] = lidx[(size_t)ip * k + j];
+    float ld[KMAX];
+    uint32_t li[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j < k) {
+        ld[j] = ldist[(size_t)ip * k + j];
+        li[j] = lidx[(size_t)ip * k + j];
+      } else {
+        ld[j] = INFINITY;
+        li[j] = 0xffffffffu;
+      }
     }
-    float wd = ld[(k - 1) * B + t];
-    uint32_t wi = li[(k - 1) * B + t];
+    float wd = INFINITY;
+    uint32_t wi = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j == k - 1) {
+        wd = ld[j];
+        wi = li[j];
+      }
     for (int side = 0; side < 2; ++side) {
-      for (int delta = 1; delta <= w; ++delta) {
+      for (int delta = dlo; delta <= wtop; ++delta) {
         float cd;
         uint32_t ci;
         if (side == 0) {  // right neighbour (p, p + delta)
           if (p + delta >= n) break;
-          cd = band[rowp * wr + delta - 1];
+          cd = band[rowp * WB + delta - dlo];
           ci = srow[rowp + delta];
         } else {  // left neighbour (p - delta, p)
           if (p - delta < 0) break;
-          cd = band[(rowp - delta) * wr + delta - 1];
+          cd = band[(rowp - delta) * WB + delta - dlo];
           ci = srow[rowp - delta];
         }
         if (!lessp(cd, ci, wd, wi)) continue;
         bool dup = false;
-        for (int j = 0; j < k; ++j) dup |= (li[j * B + t] == ci);
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) dup |= (j < k) && (li[j] == ci);
         if (dup) continue;
-        int j = k - 1;
-        while (j > 0 && lessp(cd, ci, ld[(j - 1) * B + t], li[(j - 1) * B + t])) {
-          ld[j * B + t] = ld[(j - 1) * B + t];
-          li[j * B + t] = li[(j - 1) * B + t];
-          --j;
+        bool placed = false;
+#pragma unroll
+        for (int j = KMAX - 1; j >= 0; --j) {
+          if (j < k && !placed) {
+            if (j > 0 && lessp(cd, ci, ld[j - 1], li[j - 1])) {
+              ld[j] = ld[j - 1];
+              li[j] = li[j - 1];
+            } else {
+              ld[j] = cd;
+              li[j] = ci;
+              placed = true;
+            }
+          }
         }
-        ld[j * B + t] = cd;
-        li[j * B + t] = ci;
-        wd = ld[(k - 1) * B + t];
-        wi = li[(k - 1) * B + t];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+          if (j == k - 1) {
+            wd = ld[j];
+            wi = li[j];
+          }
       }
     }
-    for (int j = 0; j < k; ++j) {
-      ldist[(size_t)ip * k + j] = ld[j * B + t];
-      lidx[(size_t)ip * k + j] = li[j * B + t];
-    }
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) {
+        ldist[(size_t)ip * k + j] = ld[j];
+        lidx[(size_t)ip * k + j] = li[j];
+      }
   }
 }
 
@@ -207,50 +232,42 @@ __global__ void list_init_kernel(uint32_t* __restrict__ idx, float* __restrict__
   }
 }
 
-size_t window_smem(int B, int wr, int k) {
-  const int NR = B + 2 * wr;
-  return ((size_t)NR * XS + (size_t)(B + wr) * wr) * sizeof(float) + (size_t)NR * 4 +
-         (size_t)k * B * 8;
+size_t window_smem(int B, int dhi) {
+  const int NR = B + 2 * dhi;
+  const size_t staging = (size_t)2 * DC * staging_pitch(NR);
+  const size_t bandf = (size_t)ROWS * WB;
+  return ((staging > bandf ? staging : bandf) + (size_t)NR) * 4;
 }
 
-template <int UPT>
-int launch_upt(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k, int B, int wr,
-               uint32_t* li, float* ldd, cudaStream_t s) {
-  const size_t smem = window_smem(B, wr, k);
-  if (cudaFuncSetAttribute((const void*)window_kernel<UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return HF_ECUDA;
-  const unsigned blocks = hf_blocks(n, B);
-  // 16-byte loads need every row start 16-byte aligned
-  const int vec4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-  window_kernel<UPT><<<blocks, WNT, smem, s>>>(x, n, d, sigma, w, k, B, wr, vec4, li, ldd); hf_after_launch("window_kernel<UPT>", s);
+template <int KMAX>
+int launch_kmax(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k, uint32_t* li,
+                float* ldd, cudaStream_t s) {
+  for (int dlo = 1; dlo <= w; dlo += WB) {
+    const int dhi = dlo + WB - 1;
+    const int B = ROWS - dhi;
+    if (B < 32) return HF_ENOTIMPL;
+    const size_t smem = window_smem(B, dhi);
+    if (smem > 227 * 1024) return HF_ENOTIMPL;
+    if (cudaFuncSetAttribute((const void*)window_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return HF_ECUDA;
+    window_kernel<KMAX><<<hf_blocks(n, B), WNT, smem, s>>>(x, n, d, sigma, w, k, B, dlo, li, ldd);
+    hf_after_launch("window_kernel", s);
+  }
   return HF_OK;
 }
 
 }  // namespace
 
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s) {
-  list_init_kernel<<<hf_blocks(count, 256, 152 * 8), 256, 0, s>>>(idx, dist, count); hf_after_launch("list_init_kernel", s);
+  list_init_kernel<<<hf_blocks(count, 256, 152 * 8), 256, 0, s>>>(idx, dist, count);
+  hf_after_launch("list_init_kernel", s);
 }
 
-// Chooses B so that (B + wr) / 4 * wr / 8 units fill a multiple of the block.
+// One launch per band of 32 offsets; w up to 448 (B >= 32).
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s) {
-  const int wr = (w + UC - 1) / UC * UC;
-  // units = (B + wr) * wr / 32; pick B (multiple of 4) for ~1..4 units/thread
-  int upt;
-  if (wr <= 32) upt = 1;
-  else if (wr <= 64) upt = 2;
-  else upt = 4;
-  if (wr > 128) return HF_ENOTIMPL;
-  int B = (upt * WNT * 32) / wr - wr;  // largest B with units <= upt * WNT
-  B = B / UR * UR;
-  if (B < 16) return HF_ENOTIMPL;
-  if (B > 512) B = 512;
-  while (window_smem(B, wr, k) > 220 * 1024 && B > 16) B -= 16;
-  switch (upt) {
-    case 1: return launch_upt<1>(x, n, d, sigma, w, k, B, wr, list_idx, list_dist, s);
-    case 2: return launch_upt<2>(x, n, d, sigma, w, k, B, wr, list_idx, list_dist, s);
-    default: return launch_upt<4>(x, n, d, sigma, w, k, B, wr, list_idx, list_dist, s);
-  }
+  if (k <= 16) return launch_kmax<16>(x, n, d, sigma, w, k, list_idx, list_dist, s);
+  if (k <= 32) return launch_kmax<32>(x, n, d, sigma, w, k, list_idx, list_dist, s);
+  return launch_kmax<64>(x, n, d, sigma, w, k, list_idx, list_dist, s);
 }
