@@ -392,45 +392,42 @@ int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
 
 int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
   if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (w > 448) return HF_ENOTIMPL;  // widest window the band launches cover
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
-  const size_t cnt = (size_t)n * k;
-  const bool dev_i = classify(out_idx) == 1, dev_d = classify(out_dist) == 1;
-  uint32_t* li = dev_i ? reinterpret_cast<uint32_t*>(out_idx) : nullptr;
-  float* ldd = dev_d ? out_dist : nullptr;
-  cudaError_t e = cudaSuccess;
-  if (!li) e = dalloc(&li, cnt);
-  if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt);
+  // the window kernel keeps the top kp >= k per point; the first k columns
+  // are the result
+  const int kp = window_list_pitch(k);
+  uint32_t* li = nullptr;
+  float* ldd = nullptr;
+  cudaError_t e = dalloc(&li, (size_t)n * kp);
+  if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp);
   if (e != cudaSuccess) {
-    if (!dev_i) dfree(li);
-    if (!dev_d) dfree(ldd);
+    dfree(li);
+    dfree(ldd);
     return map_cuda(e);
   }
   Timer tm(f, s);
   cudaEvent_t a0 = tm.mark();
-  launch_list_init(li, ldd, (int64_t)cnt, s);
+  launch_list_init(li, ldd, n * kp, s);
   int rc = HF_OK;
-  const int wmax = 128;
-  for (int t = 0; t < f->T && rc == HF_OK; ++t) {
-    // windows wider than one pass covers are split into offset bands
-    if (w > wmax) {
-      rc = HF_ENOTIMPL;
-      break;
-    }
-    rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, k, li, ldd, s);
-  }
+  for (int t = 0; t < f->T && rc == HF_OK; ++t)
+    rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(4, a0, a1);
-  if (rc == HF_OK && !dev_i)
-    rc = map_cuda(cudaMemcpyAsync(out_idx, li, cnt * 4, cudaMemcpyDeviceToHost, s));
-  if (rc == HF_OK && !dev_d)
-    rc = map_cuda(cudaMemcpyAsync(out_dist, ldd, cnt * 4, cudaMemcpyDeviceToHost, s));
+  // first k of kp columns into the caller's buffers (device or host)
+  if (rc == HF_OK)
+    rc = map_cuda(cudaMemcpy2DAsync(out_idx, (size_t)k * 4, li, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
+                                    cudaMemcpyDefault, s));
+  if (rc == HF_OK)
+    rc = map_cuda(cudaMemcpy2DAsync(out_dist, (size_t)k * 4, ldd, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
+                                    cudaMemcpyDefault, s));
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
   if (rc == HF_OK) tm.collect({4});
-  if (!dev_i) dfree(li);
-  if (!dev_d) dfree(ldd);
+  dfree(li);
+  dfree(ldd);
   return rc;
 }
 

@@ -101,7 +101,8 @@ int sort_tree(hf_forest* f, int tree, cudaStream_t s);  // keys -> sigma, prefix
 int tie_fixup_big(hf_forest* f, int tree, uint32_t big_runs, cudaStream_t s);
 
 // window.cu
-int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k,
+int window_list_pitch(int k);  // list slots per point kept by the window kernel (>= k)
+int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s);
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
 

@@ -62,6 +62,15 @@ __host__ __device__ __forceinline__ int staging_pitch(int NR) {
   return ((p >> 2) & 1) ? p : p + 4;
 }
 
+// Slot of staged row r inside a coordinate column: rows move in groups of 4
+// (one 16-byte load); group index bit 3 is folded into bit 0 so that the five
+// b-blocks a quarter-warp reads (groups 2m + q, five consecutive m) fall into
+// five different bank quads.
+__device__ __forceinline__ int rslot(int r) {
+  const int gq = r >> 2;
+  return ((gq ^ ((gq >> 3) & 1)) << 2) | (r & 3);
+}
+
 // Stage coordinates [c0, c0 + DC) of staged rows [0, NR) into buf[c][row].
 // Lanes take 16 consecutive coordinates of 2 rows: 64-byte global segments.
 __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const uint32_t* srow,
@@ -71,19 +80,63 @@ __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const u
     const uint32_t pid = srow[r];
     const bool ok = pid != 0xffffffffu && c0 + c < d;
     const float* src = ok ? x + (size_t)pid * d + c0 + c : x;
-    cp_async4(buf + c * NRP + r, src, ok);
+    cp_async4(buf + c * NRP + rslot(r), src, ok);
   }
 }
 
+// A point's list in registers: KP slots, ascending by (distance, index).
+// The graph keeps the top KP >= k per point (KP = 16, 32 or 64) so that every
+// slot index is a compile-time constant and the list stays in registers; the
+// top k of the top KP is the top k, so the caller keeps the first k columns.
+template <int KP>
+struct ListK {
+  float d[KP];
+  uint32_t i[KP];
+
+  __device__ __forceinline__ void load(const float* gd, const uint32_t* gi) {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      d[j] = gd[j];
+      i[j] = gi[j];
+    }
+  }
+  __device__ __forceinline__ void store(float* gd, uint32_t* gi) const {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      gd[j] = d[j];
+      gi[j] = i[j];
+    }
+  }
+  // Inserts (cd, ci) unless it is no better than the last slot or listed.
+  __device__ __forceinline__ void offer(float cd, uint32_t ci) {
+    if (!lessp(cd, ci, d[KP - 1], i[KP - 1])) return;
+    bool dup = false;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) dup |= (i[j] == ci);
+    if (dup) return;
+    // the candidate sinks from slot 0: at each slot the smaller stays
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const bool sw = lessp(cd, ci, d[j], i[j]);
+      const float td = sw ? d[j] : cd;
+      const uint32_t ti = sw ? i[j] : ci;
+      d[j] = sw ? cd : d[j];
+      i[j] = sw ? ci : i[j];
+      cd = td;
+      ci = ti;
+    }
+  }
+};
+
 // One band of offsets [dlo, dlo + WB - 1] for the block's positions.
-template <int KMAX>
+template <int KP>
 __global__ void __launch_bounds__(WNT, 2)
 window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sigma, int w,
-              int k, int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
+              int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   extern __shared__ __align__(16) float smem[];
   const int dhi = dlo + WB - 1;
   const int NR = B + 2 * dhi;  // staged rows
-  const int NRP = staging_pitch(NR);
+  const int NRP = staging_pitch((NR + 7) & ~7);
   float* buf0 = smem;
   float* buf1 = smem + DC * NRP;
   const int stage_floats = 2 * DC * NRP > ROWS * WB ? 2 * DC * NRP : ROWS * WB;
@@ -123,11 +176,11 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
     for (int j = 0; j < DC; ++j) {
       const float* col = cur + j * NRP;
       float a[UR], b[16];
-      *reinterpret_cast<float4*>(a) = *reinterpret_cast<const float4*>(col + pr);
-      *reinterpret_cast<float4*>(a + 4) = *reinterpret_cast<const float4*>(col + pr + 4);
+      *reinterpret_cast<float4*>(a) = *reinterpret_cast<const float4*>(col + rslot(pr));
+      *reinterpret_cast<float4*>(a + 4) = *reinterpret_cast<const float4*>(col + rslot(pr + 4));
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<float4*>(b + 4 * q) = *reinterpret_cast<const float4*>(col + br + 4 * q);
+        *reinterpret_cast<float4*>(b + 4 * q) = *reinterpret_cast<const float4*>(col + rslot(br + 4 * q));
 #pragma unroll
       for (int t = 0; t < UR; ++t)
 #pragma unroll
@@ -155,72 +208,14 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
     if (p >= n) break;
     const int rowp = tt + dhi;  // staged row of p
     const uint32_t ip = srow[rowp];
-    float ld[KMAX];
-    uint32_t li[KMAX];
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-      if (j < k) {
-        ld[j] = ldist[(size_t)ip * k + j];
-        li[j] = lidx[(size_t)ip * k + j];
-      } else {
-        ld[j] = INFINITY;
-        li[j] = 0xffffffffu;
-      }
-    }
-    float wd = INFINITY;
-    uint32_t wi = 0xffffffffu;
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j == k - 1) {
-        wd = ld[j];
-        wi = li[j];
-      }
-    for (int side = 0; side < 2; ++side) {
-      for (int delta = dlo; delta <= wtop; ++delta) {
-        float cd;
-        uint32_t ci;
-        if (side == 0) {  // right neighbour (p, p + delta)
-          if (p + delta >= n) break;
-          cd = band[rowp * WB + delta - dlo];
-          ci = srow[rowp + delta];
-        } else {  // left neighbour (p - delta, p)
-          if (p - delta < 0) break;
-          cd = band[(rowp - delta) * WB + delta - dlo];
-          ci = srow[rowp - delta];
-        }
-        if (!lessp(cd, ci, wd, wi)) continue;
-        bool dup = false;
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) dup |= (j < k) && (li[j] == ci);
-        if (dup) continue;
-        bool placed = false;
-#pragma unroll
-        for (int j = KMAX - 1; j >= 0; --j) {
-          if (j < k && !placed) {
-            if (j > 0 && lessp(cd, ci, ld[j - 1], li[j - 1])) {
-              ld[j] = ld[j - 1];
-              li[j] = li[j - 1];
-            } else {
-              ld[j] = cd;
-              li[j] = ci;
-              placed = true;
-            }
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-          if (j == k - 1) {
-            wd = ld[j];
-            wi = li[j];
-          }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j)
-      if (j < k) {
-        ldist[(size_t)ip * k + j] = ld[j];
-        lidx[(size_t)ip * k + j] = li[j];
-      }
+    ListK<KP> L;
+    L.load(ldist + (size_t)ip * KP, lidx + (size_t)ip * KP);
+    const int rmax = (int)(n - 1 - p < wtop ? n - 1 - p : wtop);  // right: (p, p + delta)
+    for (int delta = dlo; delta <= rmax; ++delta) L.offer(band[rowp * WB + delta - dlo], srow[rowp + delta]);
+    const int lmax = (int)(p < wtop ? p : wtop);  // left: (p - delta, p)
+    for (int delta = dlo; delta <= lmax; ++delta)
+      L.offer(band[(rowp - delta) * WB + delta - dlo], srow[rowp - delta]);
+    L.store(ldist + (size_t)ip * KP, lidx + (size_t)ip * KP);
   }
 }
 
@@ -234,24 +229,24 @@ __global__ void list_init_kernel(uint32_t* __restrict__ idx, float* __restrict__
 
 size_t window_smem(int B, int dhi) {
   const int NR = B + 2 * dhi;
-  const size_t staging = (size_t)2 * DC * staging_pitch(NR);
+  const size_t staging = (size_t)2 * DC * staging_pitch((NR + 7) & ~7);
   const size_t bandf = (size_t)ROWS * WB;
   return ((staging > bandf ? staging : bandf) + (size_t)NR) * 4;
 }
 
-template <int KMAX>
-int launch_kmax(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k, uint32_t* li,
-                float* ldd, cudaStream_t s) {
+template <int KP>
+int launch_kp(const float* x, int64_t n, int d, const uint32_t* sigma, int w, uint32_t* li, float* ldd,
+              cudaStream_t s) {
   for (int dlo = 1; dlo <= w; dlo += WB) {
     const int dhi = dlo + WB - 1;
     const int B = ROWS - dhi;
     if (B < 32) return HF_ENOTIMPL;
     const size_t smem = window_smem(B, dhi);
     if (smem > 227 * 1024) return HF_ENOTIMPL;
-    if (cudaFuncSetAttribute((const void*)window_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute((const void*)window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return HF_ECUDA;
-    window_kernel<KMAX><<<hf_blocks(n, B), WNT, smem, s>>>(x, n, d, sigma, w, k, B, dlo, li, ldd);
+    window_kernel<KP><<<hf_blocks(n, B), WNT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
     hf_after_launch("window_kernel", s);
   }
   return HF_OK;
@@ -264,10 +259,16 @@ void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s)
   hf_after_launch("list_init_kernel", s);
 }
 
-// One launch per band of 32 offsets; w up to 448 (B >= 32).
-int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int k,
+int window_list_pitch(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
+
+// One launch per band of 32 offsets; w up to 448 (B >= 32). Lists have
+// window_list_pitch(k) slots per point.
+int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s) {
-  if (k <= 16) return launch_kmax<16>(x, n, d, sigma, w, k, list_idx, list_dist, s);
-  if (k <= 32) return launch_kmax<32>(x, n, d, sigma, w, k, list_idx, list_dist, s);
-  return launch_kmax<64>(x, n, d, sigma, w, k, list_idx, list_dist, s);
+  switch (kp) {
+    case 16: return launch_kp<16>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 32: return launch_kp<32>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 64: return launch_kp<64>(x, n, d, sigma, w, list_idx, list_dist, s);
+    default: return HF_EINVAL;
+  }
 }
