@@ -1,0 +1,163 @@
+"""Parity at the full-size workload shape (3,000,000 x 384, the bench's launch
+configuration), on outputs the oracle can check one by one, and an exact
+oracle comparison at 200,000 x 384.
+
+At full size the oracle recomputes: every code (quantization is cheap), the
+full keys of sampled points, the order property on sampled adjacent positions
+(oracle keys of the two points must ascend by (key, index)), the lower-bound
+property of sampled query positions, and for sampled points/queries the exact
+top-k of their window candidates (taken from the orders checked above).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthdata as S
+from _helpers import check_lists
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N, D, T, W, K = 3_000_000, 384, 3, 32, 15
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2508_21682_gb300 as hf
+
+    assert torch.cuda.is_available()
+    return hf
+
+
+@pytest.fixture(scope="module")
+def full(hf):
+    x = S.gaussian_mixture(N, D, n_components=1000, seed=S.SEED_DATA)
+    q = S.mixture_queries(2000, D, n_components=1000, data_seed=S.SEED_DATA, seed=S.SEED_QUERIES)
+    xd = torch.from_numpy(x).cuda()
+    G = hf.build(xd, T=T, bits=8, seed=S.SEED_FOREST)
+    gi, gd = G.knn_graph(K, W)
+    si, sd = G.search(torch.from_numpy(q).cuda(), K, W)
+    torch.cuda.synchronize()
+    orders = [G.order(t).astype(np.int64) for t in range(T)]
+    res = dict(x=x, q=q, G=G, gi=gi.cpu().numpy(), gd=gd.cpu().numpy(), si=si.cpu().numpy(),
+               sd=sd.cpu().numpy(), orders=orders)
+    yield res
+    G.close()
+
+
+def oracle_setup(x):
+    lo, sc = O.axis_range(x, 8)
+    return lo, sc
+
+
+def test_codes_bit_exact(full):
+    x = full["x"]
+    lo, sc = oracle_setup(x)
+    got = full["G"].codes()
+    for s in range(0, N, 500_000):
+        want = O.quantize(x[s:s + 500_000], lo, sc, 8)
+        assert np.array_equal(got[s:s + 500_000].astype(np.uint16), want), f"rows {s}.."
+
+
+def test_sampled_keys_and_order(full):
+    x = full["x"]
+    lo, sc = oracle_setup(x)
+    rng = np.random.default_rng(S.SEED_SAMPLE)
+    G = full["G"]
+    for t in range(T):
+        pi, r = O.tree_params(S.SEED_FOREST, t, D)
+        sig = full["orders"][t]
+        assert np.array_equal(np.sort(sig), np.arange(N)), f"tree {t}: not a permutation"
+        # keys of sampled points
+        if t == 0:
+            keys = G.keys(0)
+            rows = rng.choice(N, 3000, replace=False)
+            want = O.hilbert_keys(O.quantize(x[rows], lo, sc, 8), pi, r, 8)
+            assert np.array_equal(keys[rows], want)
+            del keys
+        # order property on sampled adjacent positions
+        pos = rng.choice(N - 1, 4000, replace=False)
+        a, b = sig[pos], sig[pos + 1]
+        ka = O.hilbert_keys(O.quantize(x[a], lo, sc, 8), pi, r, 8)
+        kb = O.hilbert_keys(O.quantize(x[b], lo, sc, 8), pi, r, 8)
+        for i in range(len(pos)):
+            ta = tuple(int(v) for v in ka[i]) + (int(a[i]),)
+            tb = tuple(int(v) for v in kb[i]) + (int(b[i]),)
+            assert ta < tb, f"tree {t}: positions {pos[i]}, {pos[i] + 1} out of order"
+
+
+def window_rows(orders, pts, w):
+    """Window candidates of points `pts` in the given (checked) orders."""
+    out = []
+    for sig in orders:
+        inv = np.empty(N, np.int64)
+        inv[sig] = np.arange(N)
+        p = inv[pts]
+        c = np.full((len(pts), 2 * w), -1, np.int64)
+        for j, off in enumerate(list(range(-w, 0)) + list(range(1, w + 1))):
+            pp = p + off
+            ok = (pp >= 0) & (pp < N)
+            c[ok, j] = sig[pp[ok]]
+        out.append(c)
+    return np.concatenate(out, axis=1)
+
+
+def test_sampled_graph_rows(full):
+    rng = np.random.default_rng(S.SEED_SAMPLE + 1)
+    pts = np.sort(rng.choice(N, 1500, replace=False))
+    cand = window_rows(full["orders"], pts, W)
+    oi, od = O.topk_from_candidates(full["x"], pts, cand, K)
+    check_lists(full["x"], full["gi"][pts], full["gd"][pts], oi, od, owners=pts, cand=cand)
+
+
+def test_sampled_search_rows(full):
+    x, q = full["x"], full["q"]
+    lo, sc = oracle_setup(x)
+    qs = np.arange(0, 2000, 7)
+    qc = O.quantize(q[qs], lo, sc, 8)
+    G = full["G"]
+    cands = []
+    for t in range(T):
+        pi, r = O.tree_params(S.SEED_FOREST, t, D)
+        sig = full["orders"][t]
+        p = G.locate(t, torch.from_numpy(np.ascontiguousarray(q[qs])).cuda())
+        kq = O.hilbert_keys(qc, pi, r, 8)
+        # lower-bound property: key(sig[p-1]) < key(q) <= key(sig[p])
+        left = sig[np.clip(p - 1, 0, N - 1)]
+        right = sig[np.clip(p, 0, N - 1)]
+        kl = O.hilbert_keys(O.quantize(x[left], lo, sc, 8), pi, r, 8)
+        kr = O.hilbert_keys(O.quantize(x[right], lo, sc, 8), pi, r, 8)
+        for j in range(len(qs)):
+            tq = tuple(int(v) for v in kq[j])
+            if p[j] > 0:
+                assert tuple(int(v) for v in kl[j]) < tq, f"tree {t} query {qs[j]}"
+            if p[j] < N:
+                assert tq <= tuple(int(v) for v in kr[j]), f"tree {t} query {qs[j]}"
+        c = np.full((len(qs), 2 * W), -1, np.int64)
+        for jj, off in enumerate(range(-W, W)):
+            pp = p + off
+            ok = (pp >= 0) & (pp < N)
+            c[ok, jj] = sig[pp[ok]]
+        cands.append(c)
+    cand = np.concatenate(cands, axis=1)
+    oi, od = O.topk_from_candidates(x, None, cand, K, xq=q[qs])
+    check_lists(x, full["si"][qs], full["sd"][qs], oi, od, queries=q[qs], cand=cand)
+
+
+def test_exact_oracle_200k(hf):
+    """The whole path against the oracle end to end at 200,000 x 384."""
+    n, T2 = 200_000, 2
+    x = S.gaussian_mixture(n, D, n_components=1000, seed=S.SEED_DATA)
+    F = O.Forest(x, T=T2, bits=8, seed=S.SEED_FOREST)
+    G = hf.build(torch.from_numpy(x).cuda(), T=T2, bits=8, seed=S.SEED_FOREST)
+    for t in range(T2):
+        assert np.array_equal(G.order(t).astype(np.int64), F.sigma[t]), f"order of tree {t}"
+    gi, gd = G.knn_graph(K, W)
+    rows = np.arange(0, n, 97)
+    cand = O.candidate_sets(F, W)[rows]
+    oi, od = O.topk_from_candidates(x, rows, cand, K)
+    check_lists(x, gi.cpu().numpy()[rows], gd.cpu().numpy()[rows], oi, od, owners=rows, cand=cand)
+    G.close()
