@@ -66,6 +66,7 @@ def args():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=20000)
+    p.add_argument("--mode", default="plain", choices=["plain", "tensor"])
     return p.parse_args()
 
 
@@ -196,6 +197,8 @@ def run_ours(a):
 
     def step(tim=None):
         G = hf.build(xd, T=T, bits=a.bits, seed=3)
+        if a.mode == "tensor":
+            G.set_option("mode", 1)
         G.knn_graph(k, w, gi, gd)
         G.search(qd, k, w, si, sd)
         if tim is not None:
@@ -261,6 +264,8 @@ def run_ours(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G = hf.build(xh, T=T, bits=a.bits, seed=3)
+        if a.mode == "tensor":
+            G.set_option("mode", 1)
         G.knn_graph(k, w, gih, gdh)
         G.search(qh, k, w, sih, sdh)
         G.close()
@@ -294,7 +299,7 @@ def run_ours(a):
             "dtype": "f32",
             "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
             "config": {"workload": workload_name(a), "n": n, "d": d, "T": T, "bits": a.bits, "w": w, "k": k,
-                       "queries": a.nq, "mode": "plain f32",
+                       "queries": a.nq, "mode": "plain f32" if a.mode == "plain" else "bf16 tcgen05 Gram + f32 re-rank",
                        "l2": "inputs larger than L2 (points 4.6 GB per step)",
                        "parallelism": f"replicas x{ws}"},
             "recall_at_k": rec,

@@ -97,6 +97,8 @@ void destroy(hf_forest* f) {
   dfree(f->prefix);
   dfree(f->sigma);
   dfree(f->err);
+  if (f->xb) cudaFree(f->xb);
+  dfree(f->xnrm);
   delete f;
 }
 
@@ -367,7 +369,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
   if (!f || !key) return HF_EINVAL;
   std::string k(key);
   if (k == "mode") {
-    if (value != 0) return HF_EINVAL;
+    if (value != 0 && value != 1) return HF_EINVAL;
     f->mode = (int)value;
   } else if (k == "timing") {
     f->timing = value ? 1 : 0;
@@ -396,13 +398,21 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
-  // the window kernel keeps the top kp >= k per point; the first k columns
-  // are the result
-  const int kp = window_list_pitch(k);
+  // Plain mode: the window kernel keeps the top kp >= k per point by exact
+  // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= 2k by
+  // the BF16 expansion, then the re-rank orders them by exact float32
+  // distance. Either way the first k columns are the result.
+  const bool tensor = f->mode == 1 && gram_supported(f->d, w);
+  const int kp = window_list_pitch(tensor ? 2 * k : k);
   uint32_t* li = nullptr;
   float* ldd = nullptr;
   cudaError_t e = dalloc(&li, (size_t)n * kp);
   if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp);
+  if (e == cudaSuccess && tensor && !f->xb) {
+    e = cudaMalloc(&f->xb, (size_t)n * bf16_pitch(f->d) * 2);
+    if (e == cudaSuccess) e = dalloc(&f->xnrm, (size_t)n);
+    if (e == cudaSuccess) launch_prepare_bf16(f->x, n, f->d, f->xb, f->xnrm, s);
+  }
   if (e != cudaSuccess) {
     dfree(li);
     dfree(ldd);
@@ -412,8 +422,13 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   cudaEvent_t a0 = tm.mark();
   launch_list_init(li, ldd, n * kp, s);
   int rc = HF_OK;
-  for (int t = 0; t < f->T && rc == HF_OK; ++t)
-    rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
+  for (int t = 0; t < f->T && rc == HF_OK; ++t) {
+    if (tensor)
+      rc = launch_gram_window(f->xb, f->xnrm, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, f->err, s);
+    else
+      rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
+  }
+  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, kp, li, ldd, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(4, a0, a1);
   // first k of kp columns into the caller's buffers (device or host)

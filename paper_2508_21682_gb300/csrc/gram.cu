@@ -1,0 +1,418 @@
+// Window distances on the tensor cores (tcgen05), then an exact re-rank.
+//
+// Paper, Algorithm 2: candidates are the neighbours around each position of
+// every sort; the final selection is by vector distance. The distance step is
+// the only dense contraction of the path: the squared distances between the
+// B = 128 points at positions [s, s+128) of one order and the N = 128 + 2 W8
+// points at positions [s - W8, s + 128 + W8) (W8 = w rounded up to 8) are
+//   d2(p, q) = |x_p|^2 + |x_q|^2 - 2 <x_p, x_q>,
+// and the inner products of a whole block are one 128 x N Gram tile. Here the
+// tile is computed by tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation
+// in tensor memory): the N gathered rows are staged once in shared memory in
+// the 128-byte-swizzled K-major layout; the 128 owned rows are rows W8 ..
+// W8+127 of that same tile, so both operands read one copy. The epilogue reads
+// each row's band (2w columns) out of tensor memory and merges approximate
+// distances (of the BF16-rounded vectors, expanded form) into the point's
+// top-KP list, KP >= 2k.
+//
+// After the last tree, rerank_kernel recomputes every listed candidate's
+// distance in float32 with exact coordinate differences from the float32
+// points, so the expansion's cancellation and the BF16 rounding never reach
+// the result; the list is re-sorted and the first k columns are the answer.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hf_internal.cuh"
+#include "topk_list.cuh"
+
+namespace {
+
+constexpr int GB = 128;        // owned positions per block = MMA M
+constexpr int GT = 128;        // threads per block (4 warps, one per TMEM lane quarter)
+constexpr int KC = 64;         // BF16 elements per 128-byte K chunk
+constexpr uint32_t TMEM_COLS = 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Whole warp: allocates `ncols` tensor-memory columns, writes the base
+// address to *slot (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A * B^T, A: M x 16, B: N x 16, both K-major BF16 in shared memory.
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on *bar once all MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO); the leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  desc |= (uint64_t)1 << 16;                  // leading byte offset (unused): 16 B
+  desc |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 1024 B
+  desc |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  desc |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return desc;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const int sz = valid ? 16 : 0;  // 0: zero fill
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(sz) : "memory");
+}
+
+// BF16 copy of the points (row pitch dp, a multiple of 64, zero padded) and
+// the FP32 squared norms of the BF16-rounded rows.
+__global__ void prepare_bf16_kernel(const float* __restrict__ x, int64_t n, int d, int dp,
+                                    __nv_bfloat16* __restrict__ xb, float* __restrict__ nrm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float s = 0.f;
+    for (int c = lane; c < dp; c += 32) {
+      const float v = c < d ? x[i * d + c] : 0.f;
+      const __nv_bfloat16 b = __float2bfloat16_rn(v);
+      xb[i * dp + c] = b;
+      const float r = __bfloat162float(b);
+      s = fmaf(r, r, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[i] = s;
+  }
+}
+
+struct GramArgs {
+  const __nv_bfloat16* xb;
+  const float* nrm;
+  const uint32_t* sigma;
+  int64_t n;
+  int dp, w, W8, N;
+  uint32_t idesc;
+  uint32_t* lidx;
+  float* ldist;
+  int* err;
+  uint64_t spin_limit;
+};
+
+template <int KP>
+__global__ void __launch_bounds__(GT, 1) gram_window_kernel(GramArgs a) {
+  extern __shared__ unsigned char smraw[];
+  // swizzled tiles start on a 1024-byte boundary of the shared address space
+  unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+  const int N = a.N, nk = a.dp / KC;
+  uint32_t* srow = reinterpret_cast<uint32_t*>(base + (size_t)nk * N * 128);
+  float* snorm = reinterpret_cast<float*>(srow + N);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(snorm + N + (N & 1));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t s = (int64_t)blockIdx.x * GB;
+  const int64_t r0 = s - a.W8;
+
+  if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
+  for (int r = tid; r < N; r += GT) {
+    const int64_t p = r0 + r;
+    const bool ok = p >= 0 && p < a.n;
+    const uint32_t pid = ok ? __ldg(a.sigma + p) : 0xffffffffu;
+    srow[r] = pid;
+    snorm[r] = ok ? __ldg(a.nrm + pid) : 0.f;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // stage the N gathered rows, K chunk by K chunk, in the swizzled layout
+  const int pieces = N * nk * 8;
+  for (int e = tid; e < pieces; e += GT) {
+    const int r = e / (nk * 8);
+    const int rem = e - r * nk * 8;
+    const int kc = rem >> 3, j = rem & 7;
+    const uint32_t pid = srow[r];
+    const bool ok = pid != 0xffffffffu;
+    const __nv_bfloat16* src = a.xb + (ok ? (size_t)pid * a.dp + kc * KC + j * 8 : 0);
+    unsigned char* dst = base + (size_t)kc * N * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4);
+    cp_async16(dst, src, ok);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  if (tid == 0) {
+    tc_fence_after();
+    const uint32_t sb = smem_u32(base);
+    for (int kc = 0; kc < nk; ++kc) {
+      const uint32_t chunk = sb + (uint32_t)kc * N * 128;
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        const uint64_t bdesc = smem_desc(chunk + ks * 32);
+        const uint64_t adesc = smem_desc(chunk + (a.W8 >> 3) * 1024 + ks * 32);
+        mma_bf16(tmem, adesc, bdesc, a.idesc, (kc | ks) != 0);
+      }
+    }
+    mma_commit(mbar);
+  }
+  // bounded wait for the tile
+  {
+    uint64_t it = 0;
+    while (!mbar_try_wait(mbar, 0)) {
+      if (++it > a.spin_limit) {
+        s_fail = 1;
+        break;
+      }
+    }
+  }
+  tc_fence_after();
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) hf_raise(a.err, HF_ERRBIT_TIMEOUT);
+    // give in-flight MMAs a bounded chance to finish before freeing TMEM
+    uint64_t it = 0;
+    while (!mbar_try_wait(mbar, 0) && ++it < a.spin_limit) {
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    return;
+  }
+
+  // epilogue: thread = row r of the tile = TMEM lane r
+  const int r = tid;
+  const int64_t p = s + r;
+  const bool rowok = p < a.n;
+  ListK<KP> L;
+  uint32_t ip = 0;
+  if (rowok) {
+    ip = srow[r + a.W8];
+    L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+  }
+  const float np_ = snorm[r + a.W8];
+  const int cfirst = 32 * warp;                       // columns this warp's rows may need
+  const int clast = 32 * warp + 31 + 2 * a.W8;
+  for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int c = c0 + jj;
+      const int delta = c - a.W8 - r;
+      if (rowok && c < N && delta != 0 && delta >= -a.w && delta <= a.w) {
+        const uint32_t q = srow[c];
+        if (q != 0xffffffffu) {
+          const float g = __uint_as_float(v[jj]);
+          const float d2 = np_ + snorm[c] - 2.0f * g;
+          L.offer(d2, q);
+        }
+      }
+    }
+  }
+  if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+  (void)lane;
+}
+
+// Exact re-rank: one warp per point, float32 exact-difference distances of
+// the KP listed candidates (lanes split the coordinates), then the list is
+// re-sorted by (distance, index); empty slots stay (+inf, 0xffffffff).
+template <int KP>
+__global__ void rerank_kernel(const float* __restrict__ x, int64_t n, int d, uint32_t* __restrict__ lidx,
+                              float* __restrict__ ldist) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= n) return;
+  constexpr int PER = (KP + 31) / 32;
+  float dd[PER];
+  uint32_t id[PER];
+  const float* xi = x + (size_t)i * d;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    dd[u] = INFINITY;
+    id[u] = 0xffffffffu;
+  }
+  for (int slot = 0; slot < KP; ++slot) {
+    const uint32_t c = lidx[(size_t)i * KP + slot];
+    float part = 0.f;
+    if (c != 0xffffffffu) {
+      const float* xc = x + (size_t)c * d;
+      for (int j = lane; j < d; j += 32) {
+        const float e = __ldg(xi + j) - __ldg(xc + j);
+        part = fmaf(e, e, part);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((slot & 31) == lane) {
+      dd[slot >> 5] = c != 0xffffffffu ? part : INFINITY;
+      id[slot >> 5] = c;
+    }
+  }
+  // rank of each lane's entries among all KP entries by (distance, index,
+  // slot): unique even among empty slots, and the padding slots (>= KP) rank
+  // last
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int myslot = u * 32 + lane;
+    uint32_t rk = 0;
+#pragma unroll
+    for (int v = 0; v < PER; ++v)
+      for (int src = 0; src < 32; ++src) {
+        const float od = __shfl_sync(0xffffffffu, dd[v], src);
+        const uint32_t oi = __shfl_sync(0xffffffffu, id[v], src);
+        const int os = v * 32 + src;
+        const bool lt = lessp(od, oi, dd[u], id[u]) || (od == dd[u] && oi == id[u] && os < myslot);
+        rk += lt ? 1u : 0u;
+      }
+    if (myslot < KP) {
+      ldist[(size_t)i * KP + rk] = dd[u];
+      lidx[(size_t)i * KP + rk] = id[u];
+    }
+  }
+}
+
+size_t gram_smem(int N, int dp) { return (size_t)(dp / KC) * N * 128 + (size_t)N * 8 + 64 + 1024; }
+
+template <int KP>
+int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
+  if (cudaFuncSetAttribute((const void*)gram_window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return HF_ECUDA;
+  gram_window_kernel<KP><<<hf_blocks(a.n, GB), GT, smem, s>>>(a);
+  hf_after_launch("gram_window_kernel", s);
+  return HF_OK;
+}
+
+}  // namespace
+
+int gram_supported(int d, int w) {
+  const int dp = (d + KC - 1) / KC * KC;
+  const int W8 = (w + 7) / 8 * 8;
+  const int N = GB + 2 * W8;
+  return W8 <= 64 && gram_smem(N, dp) <= 220 * 1024;
+}
+
+void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s) {
+  const int dp = (d + KC - 1) / KC * KC;
+  prepare_bf16_kernel<<<hf_blocks(n * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, dp,
+                                                                      static_cast<__nv_bfloat16*>(xb), nrm);
+  hf_after_launch("prepare_bf16_kernel", s);
+}
+
+size_t bf16_pitch(int d) { return (size_t)(d + KC - 1) / KC * KC; }
+
+int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const uint32_t* sigma, int w, int kp,
+                       uint32_t* li, float* ld, int* err, cudaStream_t s) {
+  GramArgs a;
+  a.xb = static_cast<const __nv_bfloat16*>(xb);
+  a.nrm = nrm;
+  a.sigma = sigma;
+  a.n = n;
+  a.dp = (int)bf16_pitch(d);
+  a.w = w;
+  a.W8 = (w + 7) / 8 * 8;
+  a.N = GB + 2 * a.W8;
+  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.N >> 3) << 17) | ((uint32_t)(GB >> 4) << 24);
+  a.lidx = li;
+  a.ldist = ld;
+  a.err = err;
+  a.spin_limit = 1ull << 26;
+  // at most two blocks per SM so that their tensor memory (2 x 256 columns)
+  // always fits
+  size_t smem = gram_smem(a.N, a.dp);
+  if (smem < 80 * 1024) smem = 80 * 1024;
+  switch (kp) {
+    case 16: return launch_gram_kp<16>(a, smem, s);
+    case 32: return launch_gram_kp<32>(a, smem, s);
+    case 64: return launch_gram_kp<64>(a, smem, s);
+    default: return HF_EINVAL;
+  }
+}
+
+int launch_rerank(const float* x, int64_t n, int d, int kp, uint32_t* li, float* ld, cudaStream_t s) {
+  const unsigned blocks = hf_blocks(n * 32, 256);
+  switch (kp) {
+    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
+    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
+    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
+    default: return HF_EINVAL;
+  }
+  hf_after_launch("rerank_kernel", s);
+  return HF_OK;
+}

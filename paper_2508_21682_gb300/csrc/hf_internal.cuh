@@ -59,6 +59,11 @@ struct hf_forest {
 
   int* err = nullptr;         // device error word
 
+  // tensor mode: BF16 copy of the points (pitch bf16_pitch(d)) and the FP32
+  // squared norms of its rows, made on first use
+  void* xb = nullptr;
+  float* xnrm = nullptr;
+
   uint64_t* pk = nullptr;     // [K][n] key prefixes in point order (scratch)
   SortScratch sort;
   TieScratch tie;
@@ -105,6 +110,14 @@ int window_list_pitch(int k);  // list slots per point kept by the window kernel
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s);
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
+
+// gram.cu
+int gram_supported(int d, int w);
+size_t bf16_pitch(int d);
+void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s);
+int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const uint32_t* sigma, int w, int kp,
+                       uint32_t* li, float* ld, int* err, cudaStream_t s);
+int launch_rerank(const float* x, int64_t n, int d, int kp, uint32_t* li, float* ld, cudaStream_t s);
 
 // search.cu
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,

@@ -30,6 +30,7 @@
 #include <math.h>
 
 #include "hf_internal.cuh"
+#include "topk_list.cuh"
 
 namespace {
 
@@ -40,10 +41,6 @@ constexpr int UC = 8;           // offsets per unit
 constexpr int WB = 32;          // offsets per band (launch)
 constexpr int ROWS = 512;       // unit rows per block: B + dhi
 constexpr int OG = WB / UC;     // offset groups per band
-
-__device__ __forceinline__ bool lessp(float da, uint32_t ia, float db, uint32_t ib) {
-  return da < db || (da == db && ia < ib);
-}
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
@@ -84,49 +81,7 @@ __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const u
   }
 }
 
-// A point's list in registers: KP slots, ascending by (distance, index).
-// The graph keeps the top KP >= k per point (KP = 16, 32 or 64) so that every
-// slot index is a compile-time constant and the list stays in registers; the
-// top k of the top KP is the top k, so the caller keeps the first k columns.
-template <int KP>
-struct ListK {
-  float d[KP];
-  uint32_t i[KP];
 
-  __device__ __forceinline__ void load(const float* gd, const uint32_t* gi) {
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      d[j] = gd[j];
-      i[j] = gi[j];
-    }
-  }
-  __device__ __forceinline__ void store(float* gd, uint32_t* gi) const {
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      gd[j] = d[j];
-      gi[j] = i[j];
-    }
-  }
-  // Inserts (cd, ci) unless it is no better than the last slot or listed.
-  __device__ __forceinline__ void offer(float cd, uint32_t ci) {
-    if (!lessp(cd, ci, d[KP - 1], i[KP - 1])) return;
-    bool dup = false;
-#pragma unroll
-    for (int j = 0; j < KP; ++j) dup |= (i[j] == ci);
-    if (dup) return;
-    // the candidate sinks from slot 0: at each slot the smaller stays
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      const bool sw = lessp(cd, ci, d[j], i[j]);
-      const float td = sw ? d[j] : cd;
-      const uint32_t ti = sw ? i[j] : ci;
-      d[j] = sw ? cd : d[j];
-      i[j] = sw ? ci : i[j];
-      cd = td;
-      ci = ti;
-    }
-  }
-};
 
 // One band of offsets [dlo, dlo + WB - 1] for the block's positions.
 template <int KP>

@@ -210,3 +210,39 @@ def test_invalid_graph_arguments(hf):
             G.knn_graph(k, w)
         assert e.value.status == hf.HF_EINVAL
     G.close()
+
+
+# ---------------------------------------------------------------- tensor mode
+@pytest.mark.parametrize("n,d,T,w,k,mixture", [
+    (20000, 16, 8, 16, 10, False),   # tiny config
+    (6001, 384, 2, 32, 15, True),    # full-size shape, ragged tail (6001 = 46 tiles + 113)
+    (3007, 64, 3, 60, 12, True),     # w not a multiple of 8
+    (50, 8, 3, 40, 10, False),       # n < 2w + 1: one tile, mostly empty columns
+    (3000, 100, 2, 7, 5, False),     # d not a multiple of 64 (zero-padded K)
+])
+def test_tensor_mode_graph(hf, n, d, T, w, k, mixture):
+    """BF16 Gram tiles pick each point's best 2k candidates, the exact float32
+    re-rank orders them: distances must be exact (1e-5) and the lists may
+    differ from the oracle only where the BF16 estimate dropped a true top-k
+    candidate out of the best 2k (rare)."""
+    x = S.gaussian_mixture(n, d, n_components=30, seed=2) if mixture else S.unit_gaussian(n, d, seed=2)
+    G, F = build_both(hf, x, T, 8)
+    G.set_option("mode", 1)
+    gi, gd = G.knn_graph(k, w)
+    gi, gd = gi.cpu().numpy().astype(np.int64), gd.cpu().numpy()
+    oi, od = O.knn_graph(F, k, w)
+    cand = O.candidate_sets(F, w)
+    owners = np.arange(n)
+    valid = gi >= 0
+    assert np.array_equal(valid, oi >= 0)
+    true = O.sq_dist_fp64(x, np.broadcast_to(owners[:, None], gi.shape), np.where(valid, gi, -1))
+    assert np.all(np.abs(gd[valid] - true[valid]) <= RTOL * true[valid])
+    for r in range(n):
+        row = gi[r][valid[r]]
+        assert len(set(row.tolist())) == len(row) and r not in set(row.tolist())
+        assert set(row.tolist()) <= set(cand[r][cand[r] >= 0].tolist())
+        dd = gd[r][valid[r]]
+        assert np.all((dd[1:] > dd[:-1]) | ((dd[1:] == dd[:-1]) & (row[1:] > row[:-1])))
+    hits = sum(len(set(a[a >= 0].tolist()) & set(b[b >= 0].tolist())) for a, b in zip(gi, oi))
+    assert hits / max(1, int((oi >= 0).sum())) >= 0.995
+    G.close()
