@@ -160,25 +160,50 @@ struct GramArgs {
   uint64_t spin_limit;
 };
 
+constexpr int STAGES = 2;  // K chunks in flight in shared memory
+
+// Stage K chunk kc of the N gathered rows into buf (swizzled K-major layout).
+__device__ __forceinline__ void stage_kchunk(unsigned char* buf, const uint32_t* srow, int N,
+                                             const __nv_bfloat16* __restrict__ xb, int dp, int kc) {
+  for (int e = threadIdx.x; e < N * 8; e += GT) {
+    const int r = e >> 3, j = e & 7;
+    const uint32_t pid = srow[r];
+    const bool ok = pid != 0xffffffffu;
+    const __nv_bfloat16* src = xb + (ok ? (size_t)pid * dp + kc * KC + j * 8 : 0);
+    cp_async16(buf + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4), src, ok);
+  }
+}
+
+// Bounded wait on an mbarrier phase; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint64_t limit) {
+  uint64_t it = 0;
+  while (!mbar_try_wait(bar, phase))
+    if (++it > limit) return false;
+  return true;
+}
+
 template <int KP>
-__global__ void __launch_bounds__(GT, 1) gram_window_kernel(GramArgs a) {
+__global__ void __launch_bounds__(GT, 2) gram_window_kernel(GramArgs a) {
   extern __shared__ unsigned char smraw[];
   // swizzled tiles start on a 1024-byte boundary of the shared address space
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   const int N = a.N, nk = a.dp / KC;
-  uint32_t* srow = reinterpret_cast<uint32_t*>(base + (size_t)nk * N * 128);
+  const size_t stage_bytes = (size_t)N * 128;
+  uint32_t* srow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);
   float* snorm = reinterpret_cast<float*>(srow + N);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(snorm + N + (N & 1));
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* cbd = snorm + N;                                   // [GT][32] staged candidate distances
+  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + GT * 32);  // [GT][32] staged candidate ids
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(cbi + GT * 32);  // [STAGES] stage free, [STAGES] = done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + STAGES + 1);
   __shared__ int s_fail;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t s = (int64_t)blockIdx.x * GB;
   const int64_t r0 = s - a.W8;
 
   if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
   if (tid == 0) {
-    mbar_init(mbar, 1);
+    for (int i = 0; i <= STAGES; ++i) mbar_init(mbar + i, 1);
     fence_mbar_init();
     s_fail = 0;
   }
@@ -193,61 +218,55 @@ __global__ void __launch_bounds__(GT, 1) gram_window_kernel(GramArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const uint32_t sb = smem_u32(base);
 
-  // stage the N gathered rows, K chunk by K chunk, in the swizzled layout
-  const int pieces = N * nk * 8;
-  for (int e = tid; e < pieces; e += GT) {
-    const int r = e / (nk * 8);
-    const int rem = e - r * nk * 8;
-    const int kc = rem >> 3, j = rem & 7;
-    const uint32_t pid = srow[r];
-    const bool ok = pid != 0xffffffffu;
-    const __nv_bfloat16* src = a.xb + (ok ? (size_t)pid * a.dp + kc * KC + j * 8 : 0);
-    unsigned char* dst = base + (size_t)kc * N * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4);
-    cp_async16(dst, src, ok);
+  // K-chunk pipeline: chunk kc lives in stage kc % STAGES; the MMAs of chunk
+  // kc release the stage through mbar[stage] (tcgen05.commit) before chunk
+  // kc + STAGES is copied into it.
+  for (int kc = 0; kc < STAGES && kc < nk; ++kc) {
+    stage_kchunk(base + kc * stage_bytes, srow, N, a.xb, a.dp, kc);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  fence_proxy_async_smem();
-  __syncthreads();
-
-  if (tid == 0) {
-    tc_fence_after();
-    const uint32_t sb = smem_u32(base);
-    for (int kc = 0; kc < nk; ++kc) {
-      const uint32_t chunk = sb + (uint32_t)kc * N * 128;
+  bool ok_all = true;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int st = kc % STAGES;
+    if (kc + 1 < nk) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t chunk = sb + (uint32_t)(st * stage_bytes);
       for (int ks = 0; ks < KC / 16; ++ks) {
         const uint64_t bdesc = smem_desc(chunk + ks * 32);
         const uint64_t adesc = smem_desc(chunk + (a.W8 >> 3) * 1024 + ks * 32);
         mma_bf16(tmem, adesc, bdesc, a.idesc, (kc | ks) != 0);
       }
+      mma_commit(kc + 1 < nk ? mbar + st : mbar + STAGES);
     }
-    mma_commit(mbar);
-  }
-  // bounded wait for the tile
-  {
-    uint64_t it = 0;
-    while (!mbar_try_wait(mbar, 0)) {
-      if (++it > a.spin_limit) {
-        s_fail = 1;
-        break;
-      }
+    if (kc + STAGES < nk) {
+      // the stage is reused: wait until its MMAs have read it
+      if (!mbar_wait_bounded(mbar + st, (uint32_t)((kc / STAGES) & 1), a.spin_limit)) ok_all = false;
+      __syncthreads();
+      stage_kchunk(base + st * stage_bytes, srow, N, a.xb, a.dp, kc + STAGES);
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
   }
+  if (!mbar_wait_bounded(mbar + STAGES, 0, a.spin_limit)) ok_all = false;
+  if (!ok_all) s_fail = 1;
   tc_fence_after();
   __syncthreads();
   if (s_fail) {
     if (tid == 0) hf_raise(a.err, HF_ERRBIT_TIMEOUT);
-    // give in-flight MMAs a bounded chance to finish before freeing TMEM
-    uint64_t it = 0;
-    while (!mbar_try_wait(mbar, 0) && ++it < a.spin_limit) {
-    }
+    mbar_wait_bounded(mbar + STAGES, 0, a.spin_limit);  // in-flight MMAs, bounded
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
     return;
   }
 
-  // epilogue: thread = row r of the tile = TMEM lane r
+  // epilogue: thread = row r of the tile = tensor-memory lane r. Each 32-column
+  // chunk is screened against the list's last entry; the few survivors are
+  // staged in shared memory and offered one by one (one copy of the insert).
   const int r = tid;
   const int64_t p = s + r;
   const bool rowok = p < a.n;
@@ -258,24 +277,30 @@ __global__ void __launch_bounds__(GT, 1) gram_window_kernel(GramArgs a) {
     L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
   }
   const float np_ = snorm[r + a.W8];
-  const int cfirst = 32 * warp;                       // columns this warp's rows may need
+  float* mybd = cbd + r * 32;
+  uint32_t* mybi = cbi + r * 32;
+  const int cfirst = 32 * warp;
   const int clast = 32 * warp + 31 + 2 * a.W8;
   for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
     uint32_t v[32];
     tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+    const float td = L.d[KP - 1];
+    const uint32_t ti = L.i[KP - 1];
+    int m = 0;
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) {
       const int c = c0 + jj;
       const int delta = c - a.W8 - r;
-      if (rowok && c < N && delta != 0 && delta >= -a.w && delta <= a.w) {
-        const uint32_t q = srow[c];
-        if (q != 0xffffffffu) {
-          const float g = __uint_as_float(v[jj]);
-          const float d2 = np_ + snorm[c] - 2.0f * g;
-          L.offer(d2, q);
-        }
+      const uint32_t q = c < N ? srow[c] : 0xffffffffu;
+      const float d2 = np_ + (c < N ? snorm[c] : 0.f) - 2.0f * __uint_as_float(v[jj]);
+      if (rowok && delta != 0 && delta >= -a.w && delta <= a.w && q != 0xffffffffu && lessp(d2, q, td, ti)) {
+        mybd[m] = d2;
+        mybi[m] = q;
+        ++m;
       }
     }
+#pragma unroll 1
+    for (int u = 0; u < m; ++u) L.offer(mybd[u], mybi[u]);
   }
   if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
   tc_fence_before();
@@ -284,12 +309,12 @@ __global__ void __launch_bounds__(GT, 1) gram_window_kernel(GramArgs a) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
-  (void)lane;
 }
 
-// Exact re-rank: one warp per point, float32 exact-difference distances of
-// the KP listed candidates (lanes split the coordinates), then the list is
-// re-sorted by (distance, index); empty slots stay (+inf, 0xffffffff).
+// Exact re-rank: one warp per point; lane j owns list slots j, j + 32 and
+// computes their float32 exact-difference distances over the whole vector
+// (all lanes' loads in flight at once), then the KP entries are re-sorted by
+// (distance, index); empty slots stay (+inf, 0xffffffff).
 template <int KP>
 __global__ void rerank_kernel(const float* __restrict__ x, int64_t n, int d, uint32_t* __restrict__ lidx,
                               float* __restrict__ ldist) {
@@ -300,31 +325,41 @@ __global__ void rerank_kernel(const float* __restrict__ x, int64_t n, int d, uin
   float dd[PER];
   uint32_t id[PER];
   const float* xi = x + (size_t)i * d;
+  const bool v4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    dd[u] = INFINITY;
-    id[u] = 0xffffffffu;
-  }
-  for (int slot = 0; slot < KP; ++slot) {
-    const uint32_t c = lidx[(size_t)i * KP + slot];
-    float part = 0.f;
+    const int slot = u * 32 + lane;
+    const uint32_t c = slot < KP ? lidx[(size_t)i * KP + slot] : 0xffffffffu;
+    id[u] = c;
+    float acc = 0.f;
     if (c != 0xffffffffu) {
       const float* xc = x + (size_t)c * d;
-      for (int j = lane; j < d; j += 32) {
-        const float e = __ldg(xi + j) - __ldg(xc + j);
-        part = fmaf(e, e, part);
+      if (v4) {
+        for (int j = 0; j < d; j += 4) {
+          const float4 a4 = __ldg(reinterpret_cast<const float4*>(xi + j));
+          const float4 b4 = __ldg(reinterpret_cast<const float4*>(xc + j));
+          float e = a4.x - b4.x;
+          acc = fmaf(e, e, acc);
+          e = a4.y - b4.y;
+          acc = fmaf(e, e, acc);
+          e = a4.z - b4.z;
+          acc = fmaf(e, e, acc);
+          e = a4.w - b4.w;
+          acc = fmaf(e, e, acc);
+        }
+      } else {
+        for (int j = 0; j < d; ++j) {
+          const float e = __ldg(xi + j) - __ldg(xc + j);
+          acc = fmaf(e, e, acc);
+        }
       }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((slot & 31) == lane) {
-      dd[slot >> 5] = c != 0xffffffffu ? part : INFINITY;
-      id[slot >> 5] = c;
+      dd[u] = acc;
+    } else {
+      dd[u] = INFINITY;
     }
   }
   // rank of each lane's entries among all KP entries by (distance, index,
-  // slot): unique even among empty slots, and the padding slots (>= KP) rank
-  // last
+  // slot): unique even among empty slots; padding slots (>= KP) rank last
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int myslot = u * 32 + lane;
@@ -345,7 +380,10 @@ __global__ void rerank_kernel(const float* __restrict__ x, int64_t n, int d, uin
   }
 }
 
-size_t gram_smem(int N, int dp) { return (size_t)(dp / KC) * N * 128 + (size_t)N * 8 + 64 + 1024; }
+size_t gram_smem(int N, int dp) {
+  (void)dp;
+  return (size_t)STAGES * N * 128 + (size_t)N * 8 + (size_t)GT * 32 * 8 + 8 * (STAGES + 2) + 1024;
+}
 
 template <int KP>
 int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
@@ -394,7 +432,7 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
   a.err = err;
   a.spin_limit = 1ull << 26;
   // at most two blocks per SM so that their tensor memory (2 x 256 columns)
-  // always fits
+  // always fits: each block asks for at least 80 KB of shared memory
   size_t smem = gram_smem(a.N, a.dp);
   if (smem < 80 * 1024) smem = 80 * 1024;
   switch (kp) {
