@@ -428,7 +428,7 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
     else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }
-  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, kp, li, ldd, s);
+  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, f->sigma, kp, li, ldd, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(4, a0, a1);
   // first k of kp columns into the caller's buffers (device or host)

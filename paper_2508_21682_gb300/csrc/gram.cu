@@ -311,51 +311,55 @@ __global__ void __launch_bounds__(GT, 2) gram_window_kernel(GramArgs a) {
   }
 }
 
-// Exact re-rank: one warp per point; lane j owns list slots j, j + 32 and
-// computes their float32 exact-difference distances over the whole vector
-// (all lanes' loads in flight at once), then the KP entries are re-sorted by
-// (distance, index); empty slots stay (+inf, 0xffffffff).
+// Exact re-rank: one warp per point, points taken in the order of the first
+// tree (consecutive warps then share most candidate rows in L2). The lanes
+// split the coordinates (coalesced row reads) and score 8 listed candidates
+// at a time with float32 exact differences; a butterfly sum per candidate
+// gives its distance. The KP entries are then re-sorted by (distance, index);
+// empty slots stay (+inf, 0xffffffff).
 template <int KP>
-__global__ void rerank_kernel(const float* __restrict__ x, int64_t n, int d, uint32_t* __restrict__ lidx,
-                              float* __restrict__ ldist) {
-  const int lane = threadIdx.x & 31;
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= n) return;
+__global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x, int64_t n, int d,
+                                                     const uint32_t* __restrict__ order,
+                                                     uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   constexpr int PER = (KP + 31) / 32;
+  constexpr int G = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wi >= n) return;
+  const int64_t i = order ? (int64_t)__ldg(order + wi) : wi;
+  const float* xi = x + (size_t)i * d;
+  const uint32_t mine = lane < KP ? lidx[(size_t)i * KP + lane] : 0xffffffffu;
+  const uint32_t mine2 = (PER > 1 && lane + 32 < KP) ? lidx[(size_t)i * KP + lane + 32] : 0xffffffffu;
   float dd[PER];
   uint32_t id[PER];
-  const float* xi = x + (size_t)i * d;
-  const bool v4 = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+  id[0] = mine;
+  if (PER > 1) id[PER - 1] = mine2;
 #pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int slot = u * 32 + lane;
-    const uint32_t c = slot < KP ? lidx[(size_t)i * KP + slot] : 0xffffffffu;
-    id[u] = c;
-    float acc = 0.f;
-    if (c != 0xffffffffu) {
-      const float* xc = x + (size_t)c * d;
-      if (v4) {
-        for (int j = 0; j < d; j += 4) {
-          const float4 a4 = __ldg(reinterpret_cast<const float4*>(xi + j));
-          const float4 b4 = __ldg(reinterpret_cast<const float4*>(xc + j));
-          float e = a4.x - b4.x;
-          acc = fmaf(e, e, acc);
-          e = a4.y - b4.y;
-          acc = fmaf(e, e, acc);
-          e = a4.z - b4.z;
-          acc = fmaf(e, e, acc);
-          e = a4.w - b4.w;
-          acc = fmaf(e, e, acc);
+  for (int u = 0; u < PER; ++u) dd[u] = INFINITY;
+  for (int g0 = 0; g0 < KP; g0 += G) {
+    uint32_t c[G];
+    float acc[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int slot = g0 + t;
+      c[t] = __shfl_sync(0xffffffffu, slot < 32 ? mine : mine2, slot & 31);
+      acc[t] = 0.f;
+    }
+    for (int j = lane; j < d; j += 32) {
+      const float xv = __ldg(xi + j);
+#pragma unroll
+      for (int t = 0; t < G; ++t)
+        if (c[t] != 0xffffffffu) {
+          const float e = xv - __ldg(x + (size_t)c[t] * d + j);
+          acc[t] = fmaf(e, e, acc[t]);
         }
-      } else {
-        for (int j = 0; j < d; ++j) {
-          const float e = __ldg(xi + j) - __ldg(xc + j);
-          acc = fmaf(e, e, acc);
-        }
-      }
-      dd[u] = acc;
-    } else {
-      dd[u] = INFINITY;
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+      const int slot = g0 + t;
+      if (c[t] != 0xffffffffu && (slot & 31) == lane) dd[slot >> 5] = acc[t];
     }
   }
   // rank of each lane's entries among all KP entries by (distance, index,
@@ -443,12 +447,13 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
   }
 }
 
-int launch_rerank(const float* x, int64_t n, int d, int kp, uint32_t* li, float* ld, cudaStream_t s) {
+int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
+                  cudaStream_t s) {
   const unsigned blocks = hf_blocks(n * 32, 256);
   switch (kp) {
-    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
-    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
-    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, li, ld); break;
+    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
+    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
+    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
     default: return HF_EINVAL;
   }
   hf_after_launch("rerank_kernel", s);

@@ -117,7 +117,8 @@ size_t bf16_pitch(int d);
 void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s);
 int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                        uint32_t* li, float* ld, int* err, cudaStream_t s);
-int launch_rerank(const float* x, int64_t n, int d, int kp, uint32_t* li, float* ld, cudaStream_t s);
+int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
+                  cudaStream_t s);
 
 // search.cu
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,
