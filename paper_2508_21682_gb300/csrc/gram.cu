@@ -160,154 +160,230 @@ struct GramArgs {
   uint64_t spin_limit;
 };
 
-constexpr int STAGES = 2;  // K chunks in flight in shared memory
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised Gram kernel. One block per SM loops over tiles
+// (tile t = blockIdx.x + i * gridDim.x). Warp 0 (producer) writes the tile's
+// row ids and norms and gathers its rows into a ring of STAGES K-chunk
+// buffers (cp.async; each lane's copies arrive on the chunk's "full" barrier).
+// Warp 1 (MMA) issues the chunk's four K = 16 MMAs into one of two tensor-
+// memory accumulators and releases the chunk buffer through tcgen05.commit.
+// Warps 2..5 (epilogue) drain the other accumulator: each thread owns one row
+// (tensor-memory lane), screens its band and merges into the point's list.
+// Every wait on a barrier is bounded; when one gives up, the block raises the
+// error word, every role leaves its loop, and tensor memory is freed after a
+// bounded wait for MMAs in flight.
+// ---------------------------------------------------------------------------
+constexpr int STAGES = 4;
+constexpr int PT = 192;            // threads: producer, MMA, 4 epilogue warps
+constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
 
-// Stage K chunk kc of the N gathered rows into buf (swizzled K-major layout).
-__device__ __forceinline__ void stage_kchunk(unsigned char* buf, const uint32_t* srow, int N,
-                                             const __nv_bfloat16* __restrict__ xb, int dp, int kc) {
-  for (int e = threadIdx.x; e < N * 8; e += GT) {
-    const int r = e >> 3, j = e & 7;
-    const uint32_t pid = srow[r];
-    const bool ok = pid != 0xffffffffu;
-    const __nv_bfloat16* src = xb + (ok ? (size_t)pid * dp + kc * KC + j * 8 : 0);
-    cp_async16(buf + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4), src, ok);
-  }
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint64_t limit) {
-  uint64_t it = 0;
-  while (!mbar_try_wait(bar, phase))
-    if (++it > limit) return false;
+struct PersistSmem {
+  uint64_t full[STAGES], empty[STAGES];
+  uint64_t tfull[2], tempty[2], mfull[2];
+  uint32_t tslot;
+  int abort;
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (limit in nanoseconds of %globaltimer); on timeout raises the
+// error word and the block's abort flag; returns early once another role has
+// aborted.
+__device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t limit_ns, volatile int* abort,
+                                      int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  uint32_t it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 15u) == 0) {
+      if (*abort) return false;
+      if (gtimer() - t0 > limit_ns) {
+        *abort = 1;
+        hf_raise(err, HF_ERRBIT_TIMEOUT);
+        return false;
+      }
+    }
+  }
   return true;
 }
 
 template <int KP>
-__global__ void __launch_bounds__(GT, 2) gram_window_kernel(GramArgs a) {
+__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
   extern __shared__ unsigned char smraw[];
-  // swizzled tiles start on a 1024-byte boundary of the shared address space
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   const int N = a.N, nk = a.dp / KC;
   const size_t stage_bytes = (size_t)N * 128;
-  uint32_t* srow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);
-  float* snorm = reinterpret_cast<float*>(srow + N);
-  float* cbd = snorm + N;                                   // [GT][32] staged candidate distances
-  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + GT * 32);  // [GT][32] staged candidate ids
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(cbi + GT * 32);  // [STAGES] stage free, [STAGES] = done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + STAGES + 1);
-  __shared__ int s_fail;
+  uint32_t* mrow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);  // [2][N] row ids
+  float* mnorm = reinterpret_cast<float*>(mrow + 2 * N);                      // [2][N] norms
+  float* cbd = mnorm + 2 * N;                                                 // [128][32]
+  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 128 * 32);                // [128][32]
+  PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 128 * 32);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t s = (int64_t)blockIdx.x * GB;
-  const int64_t r0 = s - a.W8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (a.n + GB - 1) / GB;
+  const uint64_t lim = a.spin_limit;
 
-  if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+  if (warp == 1) tmem_alloc(&S.tslot, TMEM_ALL);
   if (tid == 0) {
-    for (int i = 0; i <= STAGES; ++i) mbar_init(mbar + i, 1);
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&S.full[i], 32);
+      mbar_init(&S.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.tfull[i], 1);
+      mbar_init(&S.tempty[i], 4);
+      mbar_init(&S.mfull[i], 1);
+    }
+    S.abort = 0;
     fence_mbar_init();
-    s_fail = 0;
-  }
-  for (int r = tid; r < N; r += GT) {
-    const int64_t p = r0 + r;
-    const bool ok = p >= 0 && p < a.n;
-    const uint32_t pid = ok ? __ldg(a.sigma + p) : 0xffffffffu;
-    srow[r] = pid;
-    snorm[r] = ok ? __ldg(a.nrm + pid) : 0.f;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t sb = smem_u32(base);
+  const uint32_t tmem = S.tslot;
+  volatile int* abort = &S.abort;
 
-  // K-chunk pipeline: chunk kc lives in stage kc % STAGES; the MMAs of chunk
-  // kc release the stage through mbar[stage] (tcgen05.commit) before chunk
-  // kc + STAGES is copied into it.
-  for (int kc = 0; kc < STAGES && kc < nk; ++kc) {
-    stage_kchunk(base + kc * stage_bytes, srow, N, a.xb, a.dp, kc);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  bool ok_all = true;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int st = kc % STAGES;
-    if (kc + 1 < nk) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t chunk = sb + (uint32_t)(st * stage_bytes);
-      for (int ks = 0; ks < KC / 16; ++ks) {
-        const uint64_t bdesc = smem_desc(chunk + ks * 32);
-        const uint64_t adesc = smem_desc(chunk + (a.W8 >> 3) * 1024 + ks * 32);
-        mma_bf16(tmem, adesc, bdesc, a.idesc, (kc | ks) != 0);
-      }
-      mma_commit(kc + 1 < nk ? mbar + st : mbar + STAGES);
-    }
-    if (kc + STAGES < nk) {
-      // the stage is reused: wait until its MMAs have read it
-      if (!mbar_wait_bounded(mbar + st, (uint32_t)((kc / STAGES) & 1), a.spin_limit)) ok_all = false;
-      __syncthreads();
-      stage_kchunk(base + st * stage_bytes, srow, N, a.xb, a.dp, kc + STAGES);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-  }
-  if (!mbar_wait_bounded(mbar + STAGES, 0, a.spin_limit)) ok_all = false;
-  if (!ok_all) s_fail = 1;
-  tc_fence_after();
-  __syncthreads();
-  if (s_fail) {
-    if (tid == 0) hf_raise(a.err, HF_ERRBIT_TIMEOUT);
-    mbar_wait_bounded(mbar + STAGES, 0, a.spin_limit);  // in-flight MMAs, bounded
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
-    return;
-  }
-
-  // epilogue: thread = row r of the tile = tensor-memory lane r. Each 32-column
-  // chunk is screened against the list's last entry; the few survivors are
-  // staged in shared memory and offered one by one (one copy of the insert).
-  const int r = tid;
-  const int64_t p = s + r;
-  const bool rowok = p < a.n;
-  ListK<KP> L;
-  uint32_t ip = 0;
-  if (rowok) {
-    ip = srow[r + a.W8];
-    L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
-  }
-  const float np_ = snorm[r + a.W8];
-  float* mybd = cbd + r * 32;
-  uint32_t* mybi = cbi + r * 32;
-  const int cfirst = 32 * warp;
-  const int clast = 32 * warp + 31 + 2 * a.W8;
-  for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
-    uint32_t v[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-    const float td = L.d[KP - 1];
-    const uint32_t ti = L.i[KP - 1];
-    int m = 0;
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-      const int c = c0 + jj;
-      const int delta = c - a.W8 - r;
-      const uint32_t q = c < N ? srow[c] : 0xffffffffu;
-      const float d2 = np_ + (c < N ? snorm[c] : 0.f) - 2.0f * __uint_as_float(v[jj]);
-      if (rowok && delta != 0 && delta >= -a.w && delta <= a.w && q != 0xffffffffu && lessp(d2, q, td, ti)) {
-        mybd[m] = d2;
-        mybi[m] = q;
-        ++m;
-      }
-    }
-#pragma unroll 1
-    for (int u = 0; u < m; ++u) L.offer(mybd[u], mybi[u]);
-  }
-  if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
-  tc_fence_before();
-  __syncthreads();
   if (warp == 0) {
+    // ---------------- producer
+    uint32_t it = 0;  // chunk counter across tiles
+    int tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      const uint32_t use = (uint32_t)(tl >> 1);
+      if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
+      uint32_t* srow = mrow + buf * N;
+      float* snorm = mnorm + buf * N;
+      const int64_t r0 = t * GB - a.W8;
+      for (int r = lane; r < N; r += 32) {
+        const int64_t p = r0 + r;
+        const bool ok = p >= 0 && p < a.n;
+        const uint32_t pid = ok ? __ldg(a.sigma + p) : 0xffffffffu;
+        srow[r] = pid;
+        snorm[r] = ok ? __ldg(a.nrm + pid) : 0.f;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.mfull[buf]);
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int st = it % STAGES;
+        if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) break;
+        unsigned char* dst0 = base + st * stage_bytes;
+        for (int e = lane; e < N * 8; e += 32) {
+          const int r = e >> 3, j = e & 7;
+          const uint32_t pid = srow[r];
+          const bool ok = pid != 0xffffffffu;
+          const __nv_bfloat16* src = a.xb + (ok ? (size_t)pid * a.dp + kc * KC + j * 8 : 0);
+          cp_async16(dst0 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4), src, ok);
+        }
+        cp_async_mbar_arrive(&S.full[st]);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one lane)
+    if (lane == 0) {
+      uint32_t it = 0;
+      int tl = 0;
+      const uint32_t sb = smem_u32(base);
+      for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
+        const int buf = tl & 1;
+        const uint32_t use = (uint32_t)(tl >> 1);
+        if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(buf * 256);
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int st = it % STAGES;
+          if (!pwait(&S.full[st], (it / STAGES) & 1, lim, abort, a.err)) break;
+          fence_proxy_async_smem();  // the chunk's cp.async writes, seen by the tensor core
+          tc_fence_after();
+          const uint32_t chunk = sb + (uint32_t)(st * stage_bytes);
+#pragma unroll
+          for (int ks = 0; ks < KC / 16; ++ks) {
+            const uint64_t bdesc = smem_desc(chunk + ks * 32);
+            const uint64_t adesc = smem_desc(chunk + (a.W8 >> 3) * 1024 + ks * 32);
+            mma_bf16(acc, adesc, bdesc, a.idesc, (kc | ks) != 0);
+          }
+          mma_commit(&S.empty[st]);
+        }
+        mma_commit(&S.tfull[buf]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: warps 2..5 own tensor-memory lane quarters
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;  // tile row = TMEM lane
+    float* mybd = cbd + r * 32;
+    uint32_t* mybi = cbi + r * 32;
+    int tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      const uint32_t use = (uint32_t)(tl >> 1);
+      if (!pwait(&S.mfull[buf], use & 1, lim, abort, a.err)) break;
+      if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
+      tc_fence_after();
+      const uint32_t* srow = mrow + buf * N;
+      const float* snorm = mnorm + buf * N;
+      const int64_t p = t * GB + r;
+      const bool rowok = p < a.n;
+      ListK<KP> L;
+      uint32_t ip = 0;
+      if (rowok) {
+        ip = srow[r + a.W8];
+        L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+      }
+      const float np_ = snorm[r + a.W8];
+      const int cfirst = 32 * quarter;
+      const int clast = 32 * quarter + 31 + 2 * a.W8;
+      for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t)(buf * 256) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+        const float td = L.d[KP - 1];
+        const uint32_t ti = L.i[KP - 1];
+        int m = 0;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int c = c0 + jj;
+          const int delta = c - a.W8 - r;
+          const uint32_t q = c < N ? srow[c] : 0xffffffffu;
+          const float d2 = np_ + (c < N ? snorm[c] : 0.f) - 2.0f * __uint_as_float(v[jj]);
+          if (rowok && delta != 0 && delta >= -a.w && delta <= a.w && q != 0xffffffffu && lessp(d2, q, td, ti)) {
+            mybd[m] = d2;
+            mybi[m] = q;
+            ++m;
+          }
+        }
+#pragma unroll 1
+        for (int u = 0; u < m; ++u) L.offer(mybd[u], mybi[u]);
+      }
+      if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.tempty[buf]);
+    }
+  }
+  // teardown: the last commit completes before tensor memory is freed
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (*abort) {
+      // MMAs may still be in flight after an abort: give them a bounded time
+      const uint64_t t0 = gtimer();
+      while (gtimer() - t0 < lim) {
+      }
+    }
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, TMEM_ALL);
   }
 }
 
@@ -386,7 +462,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x
 
 size_t gram_smem(int N, int dp) {
   (void)dp;
-  return (size_t)STAGES * N * 128 + (size_t)N * 8 + (size_t)GT * 32 * 8 + 8 * (STAGES + 2) + 1024;
+  return (size_t)STAGES * N * 128 + (size_t)2 * N * 8 + (size_t)128 * 32 * 8 + sizeof(PersistSmem) + 1024;
 }
 
 template <int KP>
@@ -394,7 +470,12 @@ int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
   if (cudaFuncSetAttribute((const void*)gram_window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
-  gram_window_kernel<KP><<<hf_blocks(a.n, GB), GT, smem, s>>>(a);
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (a.n + GB - 1) / GB;
+  const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a);
   hf_after_launch("gram_window_kernel", s);
   return HF_OK;
 }
@@ -434,11 +515,11 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
   a.lidx = li;
   a.ldist = ld;
   a.err = err;
-  a.spin_limit = 1ull << 26;
-  // at most two blocks per SM so that their tensor memory (2 x 256 columns)
-  // always fits: each block asks for at least 80 KB of shared memory
+  a.spin_limit = 2000000000ull;  // 2 s per wait (globaltimer nanoseconds)
+  // one block per SM (it holds all 512 tensor-memory columns): each block asks
+  // for more than half of the SM's shared memory
   size_t smem = gram_smem(a.N, a.dp);
-  if (smem < 80 * 1024) smem = 80 * 1024;
+  if (smem < 120 * 1024) smem = 120 * 1024;
   switch (kp) {
     case 16: return launch_gram_kp<16>(a, smem, s);
     case 32: return launch_gram_kp<32>(a, smem, s);
