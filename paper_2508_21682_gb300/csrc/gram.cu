@@ -206,6 +206,7 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t l
   const uint64_t t0 = gtimer();
   uint32_t it = 0;
   while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(64);  // leave issue slots to the warps doing work
     if ((++it & 15u) == 0) {
       if (*abort) return false;
       if (gtimer() - t0 > limit_ns) {

@@ -40,16 +40,19 @@ struct ListK {
 #pragma unroll
     for (int j = 0; j < KP; ++j) dup |= (i[j] == ci);
     if (dup) return;
-    // the candidate sinks from slot 0: at each slot the smaller stays
+    // position = number of entries below the candidate (they form a prefix);
+    // every slot then takes its new value from the old list independently
+    uint32_t below = 0;
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      const bool sw = lessp(cd, ci, d[j], i[j]);
-      const float td = sw ? d[j] : cd;
-      const uint32_t ti = sw ? i[j] : ci;
-      d[j] = sw ? cd : d[j];
-      i[j] = sw ? ci : i[j];
-      cd = td;
-      ci = ti;
+    for (int j = 0; j < KP; ++j) below += lessp(d[j], i[j], cd, ci) ? 1u : 0u;
+#pragma unroll
+    for (int j = KP - 1; j >= 0; --j) {
+      const bool shift = (uint32_t)j > below;
+      const bool here = (uint32_t)j == below;
+      const float pd = j > 0 ? d[j - 1] : cd;
+      const uint32_t pi = j > 0 ? i[j - 1] : ci;
+      d[j] = shift ? pd : (here ? cd : d[j]);
+      i[j] = shift ? pi : (here ? ci : i[j]);
     }
   }
 };
