@@ -19,6 +19,7 @@
 // distance in float32 with exact coordinate differences from the float32
 // points, so the expansion's cancellation and the BF16 rounding never reach
 // the result; the list is re-sorted and the first k columns are the answer.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -184,6 +185,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// TMA gather of 4 rows (row coordinates r0..r3, columns [c, c + 64)) of the
+// BF16 point matrix into 4 consecutive 128-byte shared-memory lines, with the
+// tensor map's 128-byte swizzle; completion is counted in bytes on *bar.
+__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, int c, int r0, int r1, int r2, int r3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 struct PersistSmem {
   uint64_t full[STAGES], empty[STAGES];
   uint64_t tfull[2], tempty[2], mfull[2];
@@ -220,7 +239,7 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t l
 }
 
 template <int KP>
-__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
+__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ unsigned char smraw[];
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   const int N = a.N, nk = a.dp / KC;
@@ -238,7 +257,7 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
   if (warp == 1) tmem_alloc(&S.tslot, TMEM_ALL);
   if (tid == 0) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&S.full[i], 32);
+      mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -256,40 +275,50 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
   volatile int* abort = &S.abort;
 
   if (warp == 0) {
-    // ---------------- producer
+    // ---------------- producer: lane 0 issues the TMA gathers
     uint32_t it = 0;  // chunk counter across tiles
     int tl = 0;
-    for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
-      if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
+      int ok = 1;
+      if (lane == 0) ok = pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       uint32_t* srow = mrow + buf * N;
       float* snorm = mnorm + buf * N;
       const int64_t r0 = t * GB - a.W8;
       for (int r = lane; r < N; r += 32) {
         const int64_t p = r0 + r;
-        const bool ok = p >= 0 && p < a.n;
-        const uint32_t pid = ok ? __ldg(a.sigma + p) : 0xffffffffu;
+        const bool okr = p >= 0 && p < a.n;
+        const uint32_t pid = okr ? __ldg(a.sigma + p) : 0xffffffffu;
         srow[r] = pid;
-        snorm[r] = ok ? __ldg(a.nrm + pid) : 0.f;
+        snorm[r] = okr ? __ldg(a.nrm + pid) : 0.f;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.mfull[buf]);
-      for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int st = it % STAGES;
-        if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) break;
-        unsigned char* dst0 = base + st * stage_bytes;
-        for (int e = lane; e < N * 8; e += 32) {
-          const int r = e >> 3, j = e & 7;
-          const uint32_t pid = srow[r];
-          const bool ok = pid != 0xffffffffu;
-          const __nv_bfloat16* src = a.xb + (ok ? (size_t)pid * a.dp + kc * KC + j * 8 : 0);
-          cp_async16(dst0 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4), src, ok);
+      if (lane == 0) {
+        mbar_arrive(&S.mfull[buf]);
+        const int oob = (int)a.n;  // rows past the end: the gather fills zeros
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int st = it % STAGES;
+          if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) {
+            ok = 0;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.full[st], (uint32_t)(N * 128));
+          unsigned char* dst0 = base + st * stage_bytes;
+          for (int g = 0; g < N / 4; ++g) {
+            int rr[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t pid = srow[4 * g + q];
+              rr[q] = pid == 0xffffffffu ? oob : (int)pid;
+            }
+            tma_gather4(dst0 + g * 512, &tmap, kc * KC, rr[0], rr[1], rr[2], rr[3], &S.full[st]);
+          }
         }
-        cp_async_mbar_arrive(&S.full[st]);
       }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == 1) {
     // ---------------- MMA issuer (one lane)
     if (lane == 0) {
@@ -305,7 +334,6 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int st = it % STAGES;
           if (!pwait(&S.full[st], (it / STAGES) & 1, lim, abort, a.err)) break;
-          fence_proxy_async_smem();  // the chunk's cp.async writes, seen by the tensor core
           tc_fence_after();
           const uint32_t chunk = sb + (uint32_t)(st * stage_bytes);
 #pragma unroll
@@ -467,7 +495,7 @@ size_t gram_smem(int N, int dp) {
 }
 
 template <int KP>
-int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
+int launch_gram_kp(const GramArgs& a, const CUtensorMap& map, size_t smem, cudaStream_t s) {
   if (cudaFuncSetAttribute((const void*)gram_window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
@@ -476,9 +504,36 @@ int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a);
+  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a, map);
   hf_after_launch("gram_window_kernel", s);
   return HF_OK;
+}
+
+// Tensor map of the BF16 point matrix [n][dp]: boxes of 64 elements x 1 row
+// (one 128-byte line per gathered row), 128-byte swizzle, zero fill outside.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_row_map(CUtensorMap* map, const void* xb, int64_t n, int dp) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return HF_ECUDA;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const cuuint64_t gdim[2] = {(cuuint64_t)dp, (cuuint64_t)n};
+  const cuuint64_t gstride[1] = {(cuuint64_t)dp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)KC, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(xb), gdim, gstride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? HF_OK : HF_ECUDA;
 }
 
 }  // namespace
@@ -521,10 +576,13 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
   // for more than half of the SM's shared memory
   size_t smem = gram_smem(a.N, a.dp);
   if (smem < 120 * 1024) smem = 120 * 1024;
+  alignas(64) CUtensorMap map;
+  const int rc = make_row_map(&map, xb, n, a.dp);
+  if (rc != HF_OK) return rc;
   switch (kp) {
-    case 16: return launch_gram_kp<16>(a, smem, s);
-    case 32: return launch_gram_kp<32>(a, smem, s);
-    case 64: return launch_gram_kp<64>(a, smem, s);
+    case 16: return launch_gram_kp<16>(a, map, smem, s);
+    case 32: return launch_gram_kp<32>(a, map, smem, s);
+    case 64: return launch_gram_kp<64>(a, map, smem, s);
     default: return HF_EINVAL;
   }
 }
