@@ -67,6 +67,7 @@ def args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=20000)
     p.add_argument("--mode", default="plain", choices=["plain", "tensor"])
+    p.add_argument("--tensor-slack", type=int, default=-1)
     return p.parse_args()
 
 
@@ -199,6 +200,7 @@ def run_ours(a):
         G = hf.build(xd, T=T, bits=a.bits, seed=3)
         if a.mode == "tensor":
             G.set_option("mode", 1)
+            G.set_option("tensor_slack", a.tensor_slack)
         G.knn_graph(k, w, gi, gd)
         G.search(qd, k, w, si, sd)
         if tim is not None:
@@ -266,6 +268,7 @@ def run_ours(a):
         G = hf.build(xh, T=T, bits=a.bits, seed=3)
         if a.mode == "tensor":
             G.set_option("mode", 1)
+            G.set_option("tensor_slack", a.tensor_slack)
         G.knn_graph(k, w, gih, gdh)
         G.search(qh, k, w, sih, sdh)
         G.close()

@@ -184,6 +184,8 @@ const char* hf_status_string(int status);
  *           float32 values; falls back to mode 0 for w > 64 or when one Gram
  *           tile (N = 128 + 2 ceil8(w) rows x ceil64(d) BF16) exceeds 220 KB of
  *           shared memory;
+ *   tensor_slack=S  in mode 1, keep k + S candidates per point for the
+ *           re-rank (rounded up to 16, 32 or 64; default S = k);
  *   timing=1  record per-phase CUDA-event timings (default 1).
  * Unknown keys or values give HF_EINVAL.
  */

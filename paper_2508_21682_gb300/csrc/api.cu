@@ -371,6 +371,9 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
   if (k == "mode") {
     if (value != 0 && value != 1) return HF_EINVAL;
     f->mode = (int)value;
+  } else if (k == "tensor_slack") {
+    if (value < -1 || value > 64) return HF_EINVAL;
+    f->tensor_slack = (int)value;
   } else if (k == "timing") {
     f->timing = value ? 1 : 0;
   } else {
@@ -403,7 +406,8 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   // the BF16 expansion, then the re-rank orders them by exact float32
   // distance. Either way the first k columns are the result.
   const bool tensor = f->mode == 1 && gram_supported(f->d, w);
-  const int kp = window_list_pitch(tensor ? 2 * k : k);
+  const int slack = f->tensor_slack < 0 ? k : f->tensor_slack;
+  const int kp = window_list_pitch(tensor ? k + slack : k);
   uint32_t* li = nullptr;
   float* ldd = nullptr;
   cudaError_t e = dalloc(&li, (size_t)n * kp);

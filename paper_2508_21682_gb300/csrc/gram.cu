@@ -168,19 +168,18 @@ struct GramArgs {
 // buffers (cp.async; each lane's copies arrive on the chunk's "full" barrier).
 // Warp 1 (MMA) issues the chunk's four K = 16 MMAs into one of two tensor-
 // memory accumulators and releases the chunk buffer through tcgen05.commit.
-// Warps 2..5 (epilogue) drain the other accumulator: each thread owns one row
-// (tensor-memory lane), screens its band and merges into the point's list.
+// Warps 2..5 and 6..9 form two epilogue groups that take alternate tiles (one
+// accumulator each), so two tiles are drained at a time: each thread owns one
+// row (tensor-memory lane), screens its band and merges into the point's
+// list.
 // Every wait on a barrier is bounded; when one gives up, the block raises the
 // error word, every role leaves its loop, and tensor memory is freed after a
 // bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
 constexpr int STAGES = 4;
-constexpr int PT = 192;            // threads: producer, MMA, 4 epilogue warps
+constexpr int PT = 320;            // threads: producer, MMA, 2 x 4 epilogue warps
 constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
 
-__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -246,9 +245,9 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   const size_t stage_bytes = (size_t)N * 128;
   uint32_t* mrow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);  // [2][N] row ids
   float* mnorm = reinterpret_cast<float*>(mrow + 2 * N);                      // [2][N] norms
-  float* cbd = mnorm + 2 * N;                                                 // [128][32]
-  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 128 * 32);                // [128][32]
-  PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 128 * 32);
+  float* cbd = mnorm + 2 * N;                                                 // [256][32]
+  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);                // [256][32]
+  PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 256 * 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (a.n + GB - 1) / GB;
@@ -349,14 +348,19 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: warps 2..5 own tensor-memory lane quarters
+    // ---------------- epilogue: group 0 = warps 2..5 (accumulator 0, even
+    // tiles), group 1 = warps 6..9 (accumulator 1, odd tiles); within a
+    // group, warp w owns tensor-memory lanes 32 (w % 4) .. + 31
+    const int grp = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
-    float* mybd = cbd + r * 32;
-    uint32_t* mybi = cbi + r * 32;
-    int tl = 0;
-    for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
-      const int buf = tl & 1;
+    const int slot = grp * 128 + r;
+    float* mybd = cbd + slot * 32;
+    uint32_t* mybi = cbi + slot * 32;
+    const int buf = grp;
+    int tl = grp;
+    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles && !*abort;
+         t += 2 * (int64_t)gridDim.x, tl += 2) {
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!pwait(&S.mfull[buf], use & 1, lim, abort, a.err)) break;
       if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x
 
 size_t gram_smem(int N, int dp) {
   (void)dp;
-  return (size_t)STAGES * N * 128 + (size_t)2 * N * 8 + (size_t)128 * 32 * 8 + sizeof(PersistSmem) + 1024;
+  return (size_t)STAGES * N * 128 + (size_t)2 * N * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
 }
 
 template <int KP>

@@ -72,6 +72,7 @@ struct hf_forest {
   int64_t spin_limit_us = 2000000;
   int test_stall = 0;
   int mode = 0;
+  int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
   int timing = 1;
 
   float timings[8] = {0};

@@ -19,18 +19,27 @@ struct ListK {
   float d[KP];
   uint32_t i[KP];
 
+  // gd, gi: the point's KP slots (16-byte aligned: KP is a multiple of 4)
   __device__ __forceinline__ void load(const float* gd, const uint32_t* gi) {
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      d[j] = gd[j];
-      i[j] = gi[j];
+    for (int j = 0; j < KP; j += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(gd + j);
+      const uint4 b = *reinterpret_cast<const uint4*>(gi + j);
+      d[j] = a.x;
+      d[j + 1] = a.y;
+      d[j + 2] = a.z;
+      d[j + 3] = a.w;
+      i[j] = b.x;
+      i[j + 1] = b.y;
+      i[j + 2] = b.z;
+      i[j + 3] = b.w;
     }
   }
   __device__ __forceinline__ void store(float* gd, uint32_t* gi) const {
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      gd[j] = d[j];
-      gi[j] = i[j];
+    for (int j = 0; j < KP; j += 4) {
+      *reinterpret_cast<float4*>(gd + j) = make_float4(d[j], d[j + 1], d[j + 2], d[j + 3]);
+      *reinterpret_cast<uint4*>(gi + j) = make_uint4(i[j], i[j + 1], i[j + 2], i[j + 3]);
     }
   }
   // Inserts (cd, ci) unless it is no better than the last slot or listed.
