@@ -163,21 +163,25 @@ struct GramArgs {
 
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised Gram kernel. One block per SM loops over tiles
-// (tile t = blockIdx.x + i * gridDim.x). Warp 0 (producer) writes the tile's
-// row ids and norms and gathers its rows into a ring of STAGES K-chunk
-// buffers (cp.async; each lane's copies arrive on the chunk's "full" barrier).
-// Warp 1 (MMA) issues the chunk's four K = 16 MMAs into one of two tensor-
-// memory accumulators and releases the chunk buffer through tcgen05.commit.
-// Warps 2..5 and 6..9 form two epilogue groups that take alternate tiles (one
-// accumulator each), so two tiles are drained at a time: each thread owns one
-// row (tensor-memory lane), screens its band and merges into the point's
+// (tile t = blockIdx.x + i * gridDim.x). Warps 0..3 (loaders) write the
+// tile's row ids and norms and gather its rows into a ring of STAGES K-chunk
+// buffers: 16-byte global loads into registers (many in flight per thread),
+// then stores into the swizzled layout, a proxy fence, and one arrival per
+// thread on the chunk's "full" barrier. Warp 4 (MMA) issues the chunk's four
+// K = 16 MMAs into one of two tensor-memory accumulators and releases the
+// chunk buffer through tcgen05.commit. Warps 5..8 and 9..12 form two epilogue
+// groups that take alternate tiles (one accumulator each): each thread owns
+// one row (tensor-memory lane), screens its band and merges into the point's
 // list.
 // Every wait on a barrier is bounded; when one gives up, the block raises the
 // error word, every role leaves its loop, and tensor memory is freed after a
 // bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
 constexpr int STAGES = 4;
-constexpr int PT = 320;            // threads: producer, MMA, 2 x 4 epilogue warps
+constexpr int LW = 4;              // loader warps (warps 0..3)
+constexpr int MW = LW;             // MMA warp
+constexpr int EW0 = LW + 1;        // first epilogue warp (two groups of 4)
+constexpr int PT = (LW + 1 + 8) * 32;
 constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -253,10 +257,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const uint64_t lim = a.spin_limit;
 
-  if (warp == 1) tmem_alloc(&S.tslot, TMEM_ALL);
+  if (warp == MW) tmem_alloc(&S.tslot, TMEM_ALL);
   if (tid == 0) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&S.full[i], 1);
+      mbar_init(&S.full[i], LW * 32);
       mbar_init(&S.empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -273,52 +277,62 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   const uint32_t tmem = S.tslot;
   volatile int* abort = &S.abort;
 
-  if (warp == 0) {
-    // ---------------- producer: lane 0 issues the TMA gathers
-    uint32_t it = 0;  // chunk counter across tiles
+  if (warp < LW) {
+    // ---------------- loaders: 128 threads
+    const int lt = tid;  // 0 .. 127
+    uint32_t it = 0;     // chunk counter across tiles
     int tl = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
-      int ok = 1;
-      if (lane == 0) ok = pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err) ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
       uint32_t* srow = mrow + buf * N;
       float* snorm = mnorm + buf * N;
       const int64_t r0 = t * GB - a.W8;
-      for (int r = lane; r < N; r += 32) {
+      for (int r = lt; r < N; r += LW * 32) {
         const int64_t p = r0 + r;
         const bool okr = p >= 0 && p < a.n;
         const uint32_t pid = okr ? __ldg(a.sigma + p) : 0xffffffffu;
         srow[r] = pid;
         snorm[r] = okr ? __ldg(a.nrm + pid) : 0.f;
       }
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&S.mfull[buf]);
-        const int oob = (int)a.n;  // rows past the end: the gather fills zeros
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int st = it % STAGES;
-          if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) {
-            ok = 0;
-            break;
-          }
-          mbar_arrive_expect_tx(&S.full[st], (uint32_t)(N * 128));
-          unsigned char* dst0 = base + st * stage_bytes;
-          for (int g = 0; g < N / 4; ++g) {
-            int rr[4];
+      asm volatile("bar.sync 1, %0;" ::"r"(LW * 32) : "memory");  // loaders only
+      if (lt == 0) mbar_arrive(&S.mfull[buf]);
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int st = it % STAGES;
+        if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) {
+          ok = false;
+          break;
+        }
+        unsigned char* dst0 = base + st * stage_bytes;
+        // N * 8 16-byte pieces; up to 16 per thread, all loads issued first
+        constexpr int PER = 16;
+        uint4 v[PER];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t pid = srow[4 * g + q];
-              rr[q] = pid == 0xffffffffu ? oob : (int)pid;
-            }
-            tma_gather4(dst0 + g * 512, &tmap, kc * KC, rr[0], rr[1], rr[2], rr[3], &S.full[st]);
+        for (int q = 0; q < PER; ++q) {
+          const int e = lt + q * LW * 32;
+          v[q] = make_uint4(0, 0, 0, 0);
+          if (e < N * 8) {
+            const uint32_t pid = srow[e >> 3];
+            if (pid != 0xffffffffu)
+              v[q] = __ldg(reinterpret_cast<const uint4*>(a.xb + (size_t)pid * a.dp + kc * KC) + (e & 7));
           }
         }
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int e = lt + q * LW * 32;
+          if (e < N * 8) {
+            const int r = e >> 3, j = e & 7;
+            *reinterpret_cast<uint4*>(dst0 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4)) = v[q];
+          }
+        }
+        fence_proxy_async_smem();  // these stores, seen by the tensor core
+        mbar_arrive(&S.full[st]);
       }
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      if (!ok) break;
     }
-  } else if (warp == 1) {
+  } else if (warp == MW) {
     // ---------------- MMA issuer (one lane)
     if (lane == 0) {
       uint32_t it = 0;
@@ -348,10 +362,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: group 0 = warps 2..5 (accumulator 0, even
-    // tiles), group 1 = warps 6..9 (accumulator 1, odd tiles); within a
+    // ---------------- epilogue: group 0 = warps 5..8 (accumulator 0, even
+    // tiles), group 1 = warps 9..12 (accumulator 1, odd tiles); within a
     // group, warp w owns tensor-memory lanes 32 (w % 4) .. + 31
-    const int grp = (warp - 2) >> 2;
+    const int grp = (warp - EW0) >> 2;
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
     const int slot = grp * 128 + r;
@@ -408,7 +422,7 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   // teardown: the last commit completes before tensor memory is freed
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == MW) {
     if (*abort) {
       // MMAs may still be in flight after an abort: give them a bounded time
       const uint64_t t0 = gtimer();
@@ -546,7 +560,7 @@ int gram_supported(int d, int w) {
   const int dp = (d + KC - 1) / KC * KC;
   const int W8 = (w + 7) / 8 * 8;
   const int N = GB + 2 * W8;
-  return W8 <= 64 && gram_smem(N, dp) <= 220 * 1024;
+  return W8 <= 64 && N * 8 <= 16 * LW * 32 && gram_smem(N, dp) <= 220 * 1024;
 }
 
 void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s) {
