@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   const size_t stage_bytes = (size_t)N * 128;
   uint32_t* mrow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);  // [2][N] row ids
   float* mnorm = reinterpret_cast<float*>(mrow + 2 * N);                      // [2][N] norms
-  float* cbd = mnorm + 2 * N;                                                 // [256][32]
-  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);                // [256][32]
+  float* cbd = mnorm + 2 * N;                                                 // [32][256]
+  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);                // [32][256]
   PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 256 * 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     const int grp = (warp - EW0) >> 2;
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;  // tile row = TMEM lane
+    // staged candidates: entry u of thread `slot` at [u][slot] (conflict-free)
     const int slot = grp * 128 + r;
-    float* mybd = cbd + slot * 32;
-    uint32_t* mybi = cbi + slot * 32;
+    float* mybd = cbd + slot;
+    uint32_t* mybi = cbi + slot;
     const int buf = grp;
     int tl = grp;
     for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles && !*abort;
@@ -405,13 +406,13 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
           const uint32_t q = c < N ? srow[c] : 0xffffffffu;
           const float d2 = np_ + (c < N ? snorm[c] : 0.f) - 2.0f * __uint_as_float(v[jj]);
           if (rowok && delta != 0 && delta >= -a.w && delta <= a.w && q != 0xffffffffu && lessp(d2, q, td, ti)) {
-            mybd[m] = d2;
-            mybi[m] = q;
+            mybd[m * 256] = d2;
+            mybi[m * 256] = q;
             ++m;
           }
         }
 #pragma unroll 1
-        for (int u = 0; u < m; ++u) L.offer(mybd[u], mybi[u]);
+        for (int u = 0; u < m; ++u) L.offer(mybd[u * 256], mybi[u * 256]);
       }
       if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
       tc_fence_before();
