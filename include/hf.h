@@ -179,13 +179,14 @@ const char* hf_status_string(int status);
  *   mode=0  plain float32 window distances (default);
  *   mode=1  tensor-core window distances: BF16 Gram tiles (tcgen05, FP32
  *           accumulation) rank the candidates, each point keeps its best
- *           2k (at most 64) by that estimate, and those are re-ranked by
+ *           k + 1 (rounded up to 16, 32 or 64; see tensor_slack) by that
+ *           estimate, and those are re-ranked by
  *           float32 exact-difference distance, so returned distances are exact
  *           float32 values; falls back to mode 0 for w > 64 or when one Gram
  *           tile (N = 128 + 2 ceil8(w) rows x ceil64(d) BF16) exceeds 220 KB of
  *           shared memory;
  *   tensor_slack=S  in mode 1, keep k + S candidates per point for the
- *           re-rank (rounded up to 16, 32 or 64; default S = k);
+ *           re-rank (rounded up to 16, 32 or 64; default S = 1);
  *   timing=1  record per-phase CUDA-event timings (default 1).
  * Unknown keys or values give HF_EINVAL.
  */

@@ -402,11 +402,11 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
   // Plain mode: the window kernel keeps the top kp >= k per point by exact
-  // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= 2k by
-  // the BF16 expansion, then the re-rank orders them by exact float32
-  // distance. Either way the first k columns are the result.
+  // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= k + 1
+  // (by default) by the BF16 expansion, then the re-rank orders them by exact
+  // float32 distance. Either way the first k columns are the result.
   const bool tensor = f->mode == 1 && gram_supported(f->d, w);
-  const int slack = f->tensor_slack < 0 ? k : f->tensor_slack;
+  const int slack = f->tensor_slack < 0 ? 1 : f->tensor_slack;
   const int kp = window_list_pitch(tensor ? k + slack : k);
   uint32_t* li = nullptr;
   float* ldd = nullptr;

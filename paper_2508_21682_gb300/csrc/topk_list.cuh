@@ -45,15 +45,24 @@ struct ListK {
   // Inserts (cd, ci) unless it is no better than the last slot or listed.
   __device__ __forceinline__ void offer(float cd, uint32_t ci) {
     if (!lessp(cd, ci, d[KP - 1], i[KP - 1])) return;
-    bool dup = false;
+    // one bit per slot, combined by balanced trees (short dependency chains)
+    uint32_t dupm[KP], lowm[KP];
 #pragma unroll
-    for (int j = 0; j < KP; ++j) dup |= (i[j] == ci);
-    if (dup) return;
-    // position = number of entries below the candidate (they form a prefix);
-    // every slot then takes its new value from the old list independently
-    uint32_t below = 0;
+    for (int j = 0; j < KP; ++j) {
+      dupm[j] = i[j] == ci ? 1u : 0u;
+      lowm[j] = lessp(d[j], i[j], cd, ci) ? 1u : 0u;
+    }
 #pragma unroll
-    for (int j = 0; j < KP; ++j) below += lessp(d[j], i[j], cd, ci) ? 1u : 0u;
+    for (int w = 1; w < KP; w <<= 1)
+#pragma unroll
+      for (int j = 0; j + w < KP; j += 2 * w) {
+        dupm[j] |= dupm[j + w];
+        lowm[j] += lowm[j + w];
+      }
+    if (dupm[0]) return;
+    // entries below the candidate form a prefix; each slot then takes its new
+    // value from the old list independently
+    const uint32_t below = lowm[0];
 #pragma unroll
     for (int j = KP - 1; j >= 0; --j) {
       const bool shift = (uint32_t)j > below;
