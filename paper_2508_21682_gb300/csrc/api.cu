@@ -13,8 +13,8 @@
 #include "hf_internal.cuh"
 
 size_t sort_status_words(int64_t n, int K);
-int tie_small_cap(int W, int d, int bits, int K);
-size_t tie_scratch_words(int W, int d, int bits, int K);
+int tie_small_cap(int W, int d, int bits, int K, int K2);
+size_t tie_scratch_words(int W, int d, int bits, int K, int K2);
 
 namespace {
 
@@ -257,6 +257,10 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   {
     const int64_t need = ((int64_t)64 * f->K + d - 1) / d;
     f->L = (int)(need < bits ? need : bits);
+    // words past the sorted prefix that come from the same L top levels are
+    // computed with it (up to four): they settle equal prefixes cheaply
+    f->K2 = f->K;
+    while (f->K2 < f->W && f->K2 < f->K + 4 && (int64_t)64 * (f->K2 + 1) <= (int64_t)d * f->L) ++f->K2;
   }
   cudaGetDevice(&f->device);
 
@@ -283,19 +287,19 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   chk(dalloc(&f->prefix, (size_t)T * K * n));
   chk(dalloc(&f->sigma, (size_t)T * n));
   chk(dalloc(&f->err, 1));
-  chk(dalloc(&f->pk, (size_t)K * n));
+  chk(dalloc(&f->pk, (size_t)f->K2 * n));
   chk(dalloc(&f->sort.keys_a, n));
   chk(dalloc(&f->sort.keys_b, n));
   chk(dalloc(&f->sort.vals_a, n));
   chk(dalloc(&f->sort.vals_b, n));
   chk(dalloc(&f->sort.status, sort_status_words(n, K)));
   chk(dalloc(&f->sort.hist, (size_t)K * 8 * 256));
-  const int cap = tie_small_cap(f->W, d, bits, K);
+  const int cap = tie_small_cap(f->W, d, bits, K, f->K2);
   f->tie.big_cap = n / (cap + 1) + 1;
   chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1)));
   chk(dalloc(&f->tie.big_runs, (size_t)T * f->tie.big_cap));
   chk(dalloc(&f->tie.counters, (size_t)T * 4));
-  chk(dalloc(&f->tie.fk, K < f->W ? tie_scratch_words(f->W, d, bits, K) : 1));
+  chk(dalloc(&f->tie.fk, K < f->W ? tie_scratch_words(f->W, d, bits, K, f->K2) : 1));
   void* rscratch = nullptr;
   const size_t rbytes = range_scratch_bytes(n, d);
   chk(cudaMalloc(&rscratch, rbytes));
@@ -326,7 +330,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   tm.span(0, a0, a1);
   for (int t = 0; t < T && rc == HF_OK; ++t) {
     cudaEvent_t k0 = tm.mark();
-    launch_prefix_keys(f->planes, n, d, bits, K, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32, f->pk, s);
+    launch_prefix_keys(f->planes, n, d, bits, f->K2, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32, f->pk, s);
     cudaEvent_t k1 = tm.mark();
     rc = sort_tree(f, t, s);
     cudaEvent_t k2 = tm.mark();

@@ -43,6 +43,7 @@ struct hf_forest {
   int device = 0;
   int64_t n = 0;
   int d = 0, T = 0, bits = 0, W = 0, K = 0, L = 0, W32 = 0;
+  int K2 = 0;  // key words computed per point (K sorted + up to 4 tie-breakers)
   uint64_t seed = 0;
 
   const float* x = nullptr;  // n x d float32, device
@@ -64,7 +65,7 @@ struct hf_forest {
   void* xb = nullptr;
   float* xnrm = nullptr;
 
-  uint64_t* pk = nullptr;     // [K][n] key prefixes in point order (scratch)
+  uint64_t* pk = nullptr;     // [K2][n] key words in point order (scratch)
   SortScratch sort;
   TieScratch tie;
 

@@ -88,8 +88,9 @@ __device__ __forceinline__ uint32_t quantize_one(float x, float lo, float scale,
   return (uint32_t)cl;
 }
 
-// One warp per (point, 32-coordinate word). Lane j quantizes coordinate
-// 32m + j; a ballot per bit level gives the plane words directly.
+// One warp per point, 32 coordinates per step. Lane j quantizes coordinate
+// 32m + j; a ballot per bit level gives the plane words directly, and lane l
+// stores plane l's word.
 __global__ void quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32,
                                        const float* __restrict__ lo,
                                        const float* __restrict__ scale, int bits,
@@ -97,16 +98,18 @@ __global__ void quantize_planes_kernel(const float* __restrict__ x, int64_t n, i
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t total = n * W32;
-  for (int64_t wk = warp; wk < total; wk += nwarps) {
-    const int64_t i = wk / W32;
-    const int m = (int)(wk - i * W32);
-    const int c = m * 32 + lane;
-    uint32_t code = 0;
-    if (c < d) code = quantize_one(__ldg(x + i * d + c), __ldg(lo + c), __ldg(scale + c), bits);
-    for (int l = 0; l < bits; ++l) {
-      const uint32_t word = __ballot_sync(0xffffffffu, (code >> (bits - 1 - l)) & 1u);
-      if (lane == l) planes[((size_t)l * n + i) * W32 + m] = word;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const float* row = x + i * d;
+    for (int m = 0; m < W32; ++m) {
+      const int c = m * 32 + lane;
+      uint32_t code = 0;
+      if (c < d) code = quantize_one(__ldg(row + c), __ldg(lo + c), __ldg(scale + c), bits);
+      uint32_t mine = 0;
+      for (int l = 0; l < bits; ++l) {
+        const uint32_t word = __ballot_sync(0xffffffffu, (code >> (bits - 1 - l)) & 1u);
+        if (lane == l) mine = word;
+      }
+      if (lane < bits) planes[((size_t)lane * n + i) * W32 + m] = mine;
     }
   }
 }
@@ -182,8 +185,7 @@ void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, c
                             int bits, uint32_t* planes, int* err, cudaStream_t s) {
   (void)err;
   const int W32 = (d + 31) / 32;
-  const int64_t warps = n * W32;
-  quantize_planes_kernel<<<hf_blocks(warps * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, W32, lo, scale,
+  quantize_planes_kernel<<<hf_blocks(n * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, W32, lo, scale,
                                                                              bits, planes); hf_after_launch("quantize_planes_kernel", s);
 }
 

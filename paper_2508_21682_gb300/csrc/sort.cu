@@ -308,16 +308,17 @@ __device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const 
 
 // One block per small run (grid-stride over runs). The run's prefixes (words
 // 0..K-1) are equal, so the order inside it is decided by the following key
-// words. Words K..K2-1 lie in the top Lf bit levels, and the top Lf levels of
-// a key equal the Lf-bit key of the coordinates' top Lf bits, so they cost a
-// transform with Lf levels only (at d = 384, K2 = 6: Lf = 1, a running XOR).
+// words K..K2-1. When the key kernel computed them (kpre > K) they are read
+// from pkx[w][point]; otherwise they are computed here: they lie in the top
+// Lf bit levels, and the top Lf levels of a key equal the Lf-bit key of the
+// coordinates' top Lf bits, so they cost a transform with Lf levels only.
 // Each point's rank = number of run members below it by (words K..K2-1,
-// index). Only if two members also tie on those words does the block
-// compute full keys (into its own slice of global scratch) and rank by
-// (full key, index). Shared layout: tk[cap][K2-K], pt[cap], rank[cap],
-// Y[blockDim][d] bytes.
+// index). Only if two members also tie on those words does the block compute
+// full keys (into its own slice of global scratch) and rank by (full key,
+// index). Shared layout: tk[cap][K2-K], pt[cap], rank[cap], Y[blockDim][d].
 __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32,
                                  int bits, int W, int K, int K2, int Lf, int cap,
+                                 const uint64_t* __restrict__ pkx, int kpre,
                                  const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
                                  const uint2* __restrict__ runs, const uint32_t* __restrict__ counters,
                                  uint32_t* __restrict__ sigma, uint64_t* __restrict__ fk_scratch,
@@ -340,9 +341,13 @@ __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n,
       const uint32_t p = sigma[run.x + e];
       pt[e] = p;
       if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
-      hf_load_coords_planes(planes, n, d, W32, Lf, pi, rbits, p, Y);
-      hf_skilling(Y, d, Lf);
-      for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = hf_pack_word(Y, d, Lf, K + w);
+      if (kpre > K) {
+        for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = __ldg(pkx + (size_t)(K + w) * n + p);
+      } else {
+        hf_load_coords_planes(planes, n, d, W32, Lf, pi, rbits, p, Y);
+        hf_skilling(Y, d, Lf);
+        for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = hf_pack_word(Y, d, Lf, K + w);
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < len; e += blockDim.x) {
@@ -459,9 +464,10 @@ struct TieGeom {
 };
 
 // Words K..K2-1 (up to four) break ties; they lie in the top Lf levels.
-TieGeom tie_geom(int W, int d, int bits, int K) {
+// With kpre > K the key kernel already computed words K..kpre-1.
+TieGeom tie_geom(int W, int d, int bits, int K, int kpre) {
   TieGeom g;
-  g.K2 = K + 4 < W ? K + 4 : W;
+  g.K2 = kpre > K ? kpre : (K + 4 < W ? K + 4 : W);
   const int64_t lf = ((int64_t)64 * g.K2 + d - 1) / d;
   g.Lf = (int)(lf < bits ? lf : bits);
   const int KT = g.K2 - K;
@@ -538,7 +544,7 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
   // With K == W the prefix is the whole key: equal prefixes are equal keys,
   // already in index order.
   if (K < f->W) {
-    const TieGeom tg = tie_geom(f->W, f->d, f->bits, K);
+    const TieGeom tg = tie_geom(f->W, f->d, f->bits, K, f->K2);
     uint32_t* ctr = f->tie.counters + (size_t)t * 4;
     cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
     tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, tg.cap, f->tie.runs,
@@ -547,7 +553,7 @@ int sort_tree(hf_forest* f, int t, cudaStream_t s) {
     hf_after_launch("tie_find_kernel", s);
     set_attr((const void*)tie_small_kernel, tg.smem);
     tie_small_kernel<<<TIE_BLOCKS, TIE_THREADS, tg.smem, s>>>(
-        f->planes, n, f->d, f->W32, f->bits, f->W, K, tg.K2, tg.Lf, tg.cap, f->pi + (size_t)t * f->d,
+        f->planes, n, f->d, f->W32, f->bits, f->W, K, tg.K2, tg.Lf, tg.cap, f->pk, f->K2, f->pi + (size_t)t * f->d,
         f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->tie.fk, f->err);
     hf_after_launch("tie_small_kernel", s);
   }
@@ -608,8 +614,8 @@ int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
   return rc;
 }
 
-size_t tie_scratch_words(int W, int d, int bits, int K) {
-  const TieGeom g = tie_geom(W, d, bits, K);
+size_t tie_scratch_words(int W, int d, int bits, int K, int K2) {
+  const TieGeom g = tie_geom(W, d, bits, K, K2);
   return (size_t)TIE_BLOCKS * g.cap * W;
 }
 
@@ -618,4 +624,4 @@ size_t sort_status_words(int64_t n, int K) {
   return ((size_t)(ntiles + 1) * 256 + 1) * 8 * K;
 }
 
-int tie_small_cap(int W, int d, int bits, int K) { return tie_geom(W, d, bits, K).cap; }
+int tie_small_cap(int W, int d, int bits, int K, int K2) { return tie_geom(W, d, bits, K, K2).cap; }
