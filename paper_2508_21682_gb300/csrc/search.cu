@@ -9,11 +9,13 @@
 //
 // One warp per query, looping over the trees, so the query's top-k list stays
 // in shared memory for the whole search. Per tree, lane 0 computes the query's
-// key prefix, binary-searches the sorted prefixes, and, when the query's
-// prefix equals some data prefixes, refines the position inside that run by
-// comparing full keys (computed on demand from the bit planes). The warp then
-// scores the 2w window candidates (lanes split the coordinates, a butterfly
-// sum gives the distance) and lane 0 merges them into the list.
+// key prefix; the warp locates it among the sorted prefixes with 32-way
+// probing rounds; when the query's prefix equals some data prefixes, lane 0
+// refines the position inside that run by comparing full keys (computed on
+// demand from the bit planes). The window's candidates are scored 32 at a
+// time, one per lane over the whole vector (sequential float32 sum with exact
+// differences), sorted across the warp, and merged in ascending order until
+// the first one that cannot enter the list.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -70,7 +72,60 @@ struct SearchArgs {
   float* out_dist;
   int64_t* out_pos;
   int only_tree;
+  int vec4;  // d % 4 == 0 and both matrices 16-byte aligned
 };
+
+// Warp-wide lower bound over the sorted prefixes: each round the 32 lanes
+// probe 32 evenly spaced positions of [lo, hi) (one round trip), a ballot
+// keeps the sub-interval that holds the first position whose prefix is not
+// below the query's (le = false) or above it (le = true). About log32(n)
+// rounds instead of log2(n) dependent steps.
+__device__ __forceinline__ int64_t warp_bound(const uint64_t* __restrict__ pre, int64_t n, int K, const uint64_t* qp,
+                                              bool le, int lane) {
+  int64_t lo = 0, hi = n;  // answer in [lo, hi]
+  while (hi - lo > 0) {
+    const int64_t len = hi - lo;
+    const int64_t step = (len + 31) / 32;
+    const int64_t m = lo + (int64_t)lane * step;
+    bool below = false;  // position m lies before the answer
+    if (m < hi) {
+      const int c = cmp_prefix(pre, n, K, m, qp);
+      below = le ? (c <= 0) : (c < 0);
+    }
+    const uint32_t bm = __ballot_sync(0xffffffffu, below);
+    const int cnt = __popc(bm);  // lanes 0 .. cnt-1 are below (monotone)
+    if (cnt == 0) {
+      hi = lo;
+    } else {
+      const int64_t mlast = lo + (int64_t)(cnt - 1) * step;
+      const int64_t nhi = lo + (int64_t)cnt * step;
+      lo = mlast + 1;
+      hi = nhi < hi ? nhi : hi;
+    }
+  }
+  return lo;
+}
+
+// Bitonic sort of one (distance, index) pair per lane across the warp,
+// ascending by (distance, index).
+__device__ __forceinline__ void warp_sort(float& dv, uint32_t& iv, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, dv, j);
+      const uint32_t oi = __shfl_xor_sync(0xffffffffu, iv, j);
+      const bool up = (lane & kk) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool other_less = lessp(od, oi, dv, iv);
+      const bool take = (lower == up) ? other_less : !other_less && !(od == dv && oi == iv);
+      if (take) {
+        dv = od;
+        iv = oi;
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -101,25 +156,18 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
     const uint32_t* rb = a.rbits + (size_t)t * a.W32;
     const uint64_t* pre = a.prefix + (size_t)t * a.K * a.n;
     const uint32_t* sig = a.sigma + (size_t)t * a.n;
-    int64_t pos = 0;
     if (lane == 0) {
       hf_load_coords_codes(qc, a.d, a.bits, a.L, pi, rb, Yq);
       hf_skilling(Yq, a.d, a.L);
       for (int w = 0; w < a.K; ++w) qp[w] = hf_pack_word(Yq, a.d, a.L, w);
-      // [lo, hi): positions whose prefix equals the query's
-      int64_t lo = 0, hi = a.n;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (cmp_prefix(pre, a.n, a.K, mid, qp) < 0) lo = mid + 1;
-        else hi = mid;
-      }
-      int64_t lo2 = lo, hi2 = a.n;
-      while (lo2 < hi2) {
-        const int64_t mid = (lo2 + hi2) >> 1;
-        if (cmp_prefix(pre, a.n, a.K, mid, qp) <= 0) lo2 = mid + 1;
-        else hi2 = mid;
-      }
-      if (lo2 > lo && a.K < a.W) {
+    }
+    __syncwarp();
+    // [lo, lo2): positions whose prefix equals the query's
+    int64_t lo = warp_bound(pre, a.n, a.K, qp, false, lane);
+    const int64_t lo2 = warp_bound(pre, a.n, a.K, qp, true, lane);
+    int64_t pos = lo;
+    if (lo2 > lo && a.K < a.W) {
+      if (lane == 0) {
         // equal prefixes: lower bound by full key inside [lo, lo2)
         hf_load_coords_codes(qc, a.d, a.bits, a.bits, pi, rb, Yq);
         hf_skilling(Yq, a.d, a.bits);
@@ -131,46 +179,69 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
           if (full_key_less(Yd, Yq, a.d, a.bits, a.W)) l = mid + 1;
           else h = mid;
         }
-        lo = l;
+        pos = l;
       }
-      pos = lo;
+      pos = __shfl_sync(0xffffffffu, pos, 0);
     }
-    pos = __shfl_sync(0xffffffffu, pos, 0);
     if (a.only_tree >= 0) {
       if (lane == 0) a.out_pos[qi] = pos;
       continue;
     }
     const int64_t c0 = pos - a.w > 0 ? pos - a.w : 0;
     const int64_t c1 = pos + a.w < a.n ? pos + a.w : a.n;
-    for (int64_t c = c0; c < c1; ++c) {
-      const uint32_t pid = __ldg(sig + c);
-      const float* xv = a.x + (size_t)pid * a.d;
-      float part = 0.f;
-      for (int j = lane; j < a.d; j += 32) {
-        const float e = __ldg(qv + j) - __ldg(xv + j);
-        part = fmaf(e, e, part);
+    for (int64_t cb = c0; cb < c1; cb += 32) {
+      // lane j scores candidate cb + j over the whole vector
+      const int64_t c = cb + lane;
+      float dist = INFINITY;
+      uint32_t pid = 0xffffffffu;
+      if (c < c1) {
+        pid = __ldg(sig + c);
+        const float* xv = a.x + (size_t)pid * a.d;
+        float acc = 0.f;
+        if (a.vec4) {
+          for (int j = 0; j < a.d; j += 4) {
+            const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + j));
+            const float4 xa = __ldg(reinterpret_cast<const float4*>(xv + j));
+            float e = qa.x - xa.x;
+            acc = fmaf(e, e, acc);
+            e = qa.y - xa.y;
+            acc = fmaf(e, e, acc);
+            e = qa.z - xa.z;
+            acc = fmaf(e, e, acc);
+            e = qa.w - xa.w;
+            acc = fmaf(e, e, acc);
+          }
+        } else {
+          for (int j = 0; j < a.d; ++j) {
+            const float e = __ldg(qv + j) - __ldg(xv + j);
+            acc = fmaf(e, e, acc);
+          }
+        }
+        dist = acc;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) {
-        const float wd = ldst[a.k - 1];
-        const uint32_t wi = lidx[a.k - 1];
-        if (lessp(part, pid, wd, wi)) {
+      warp_sort(dist, pid, lane);
+      // merge in ascending order; stop at the first that cannot enter
+      for (int u = 0; u < 32; ++u) {
+        const float cd = __shfl_sync(0xffffffffu, dist, u);
+        const uint32_t ci = __shfl_sync(0xffffffffu, pid, u);
+        if (ci == 0xffffffffu) break;
+        if (!lessp(cd, ci, ldst[a.k - 1], lidx[a.k - 1])) break;
+        if (lane == 0) {
           bool dup = false;
-          for (int j = 0; j < a.k; ++j) dup |= (lidx[j] == pid);
+          for (int j = 0; j < a.k; ++j) dup |= (lidx[j] == ci);
           if (!dup) {
             int j = a.k - 1;
-            while (j > 0 && lessp(part, pid, ldst[j - 1], lidx[j - 1])) {
+            while (j > 0 && lessp(cd, ci, ldst[j - 1], lidx[j - 1])) {
               ldst[j] = ldst[j - 1];
               lidx[j] = lidx[j - 1];
               --j;
             }
-            ldst[j] = part;
-            lidx[j] = pid;
+            ldst[j] = cd;
+            lidx[j] = ci;
           }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   if (a.only_tree >= 0) return;
@@ -209,6 +280,8 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
   a.out_dist = out_dist;
   a.out_pos = out_pos;
   a.only_tree = only_tree;
+  a.vec4 = (f->d % 4 == 0) && ((reinterpret_cast<uintptr_t>(f->x) & 15) == 0) &&
+           ((reinterpret_cast<uintptr_t>(q) & 15) == 0);
   const size_t smem = search_per_warp(k, f->K, f->d) * SWARPS;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute((const void*)search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
