@@ -73,7 +73,24 @@ struct SearchArgs {
   int64_t* out_pos;
   int only_tree;
   int vec4;  // d % 4 == 0 and both matrices 16-byte aligned
+  const uint64_t* qkeys;  // [nq][T][K] query key prefixes, or null: computed in the search kernel
 };
+
+// Key prefixes of every (query, tree) pair, one thread each, so the search
+// kernel's lanes do not wait on a serial transform.
+__global__ void query_keys_kernel(const uint8_t* __restrict__ qcodes, int64_t nq, int d, int bits, int K, int L,
+                                  int T, int W32, const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
+                                  uint64_t* __restrict__ out) {
+  extern __shared__ uint8_t smy[];
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nq * T) return;
+  const int64_t qi = e / T;
+  const int t = (int)(e - qi * T);
+  uint8_t* Y = smy + (size_t)threadIdx.x * d;
+  hf_load_coords_codes(qcodes + (size_t)qi * d, d, bits, L, pi + (size_t)t * d, rbits + (size_t)t * W32, Y);
+  hf_skilling(Y, d, L);
+  for (int w = 0; w < K; ++w) out[(size_t)e * K + w] = hf_pack_word(Y, d, L, w);
+}
 
 // Warp-wide lower bound over the sorted prefixes: each round the 32 lanes
 // probe 32 evenly spaced positions of [lo, hi) (one round trip), a ballot
@@ -156,7 +173,9 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
     const uint32_t* rb = a.rbits + (size_t)t * a.W32;
     const uint64_t* pre = a.prefix + (size_t)t * a.K * a.n;
     const uint32_t* sig = a.sigma + (size_t)t * a.n;
-    if (lane == 0) {
+    if (a.qkeys) {
+      if (lane < a.K) qp[lane] = __ldg(a.qkeys + ((size_t)qi * a.T + t) * a.K + lane);
+    } else if (lane == 0) {
       hf_load_coords_codes(qc, a.d, a.bits, a.L, pi, rb, Yq);
       hf_skilling(Yq, a.d, a.L);
       for (int w = 0; w < a.K; ++w) qp[w] = hf_pack_word(Yq, a.d, a.L, w);
@@ -255,8 +274,21 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
 }  // namespace
 
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k, int w,
-                  uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree, cudaStream_t s) {
+                  uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree, cudaStream_t s,
+                  uint64_t* qkeys) {
   SearchArgs a;
+  a.qkeys = nullptr;
+  if (qkeys && only_tree < 0) {
+    int t = 256;
+    while (t > 32 && (size_t)t * f->d > 96 * 1024) t >>= 1;
+    const size_t sm = (size_t)t * f->d;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute((const void*)query_keys_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    query_keys_kernel<<<hf_blocks(nq * f->T, t), t, sm, s>>>(qcodes, nq, f->d, f->bits, f->K, f->L, f->T, f->W32,
+                                                               f->pi, f->rbits, qkeys);
+    hf_after_launch("query_keys_kernel", s);
+    a.qkeys = qkeys;
+  }
   a.x = f->x;
   a.n = f->n;
   a.d = f->d;
