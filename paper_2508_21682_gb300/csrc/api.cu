@@ -467,13 +467,11 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
   const bool dev_i = classify(out_idx) == 1, dev_d = classify(out_dist) == 1;
   float* qd = nullptr;
   uint8_t* qc = nullptr;
-  uint64_t* qk = nullptr;
   uint32_t* li = dev_i ? reinterpret_cast<uint32_t*>(out_idx) : nullptr;
   float* ldd = dev_d ? out_dist : nullptr;
   cudaError_t e = cudaSuccess;
   if (!dev_q) e = dalloc(&qd, (size_t)nq * d);
   if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d);
-  if (e == cudaSuccess) e = dalloc(&qk, (size_t)nq * f->T * f->K);
   if (e == cudaSuccess && !li) e = dalloc(&li, cnt);
   if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt);
   int rc = map_cuda(e);
@@ -483,7 +481,7 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
     const float* qsrc = dev_q ? queries : qd;
     cudaEvent_t a0 = tm.mark();
     launch_quantize_codes(qsrc, nq, d, f->lo, f->scale, f->bits, qc, f->err, s);
-    if (rc == HF_OK) rc = launch_search(f, qsrc, qc, nq, k, w, li, ldd, nullptr, -1, s, qk);
+    if (rc == HF_OK) rc = launch_search(f, qsrc, qc, nq, k, w, li, ldd, nullptr, -1, s);
     cudaEvent_t a1 = tm.mark();
     tm.span(5, a0, a1);
     if (rc == HF_OK && !dev_i) rc = map_cuda(cudaMemcpyAsync(out_idx, li, cnt * 4, cudaMemcpyDeviceToHost, s));
@@ -494,7 +492,6 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
   }
   dfree(qd);
   dfree(qc);
-  dfree(qk);
   if (!dev_i) dfree(li);
   if (!dev_d) dfree(ldd);
   return rc;

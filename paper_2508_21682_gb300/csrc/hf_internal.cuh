@@ -123,12 +123,9 @@ int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int k
                   cudaStream_t s);
 
 // search.cu
-// qkeys: optional scratch of nq * T * K words for the queries' key prefixes
-// (computed up front by a separate kernel); null computes them in the search
-// kernel.
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,
                   int w, uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree,
-                  cudaStream_t s, uint64_t* qkeys = nullptr);
+                  cudaStream_t s);
 
 // host helpers (api.cu)
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);

@@ -7,15 +7,23 @@
 // on the CPU; here every query is located independently, which parallelises
 // trivially.
 //
-// One warp per query, looping over the trees, so the query's top-k list stays
-// in shared memory for the whole search. Per tree, lane 0 computes the query's
-// key prefix; the warp locates it among the sorted prefixes with 32-way
-// probing rounds; when the query's prefix equals some data prefixes, lane 0
-// refines the position inside that run by comparing full keys (computed on
-// demand from the bit planes). The window's candidates are scored 32 at a
-// time, one per lane over the whole vector (sequential float32 sum with exact
-// differences), sorted across the warp, and merged in ascending order until
-// the first one that cannot enter the list.
+// One warp per query, looping over the trees; the query's top-k list lives in
+// registers across the warp (entry e in lane e % 32, slot e / 32).
+//  * Key prefix: when the first K key words lie in the top bit level (d >=
+//    64K) the warp forms them with ballots (running XOR of the permuted,
+//    reflected top bits); otherwise lane 0 runs the transform.
+//  * Locate: 32-way probing rounds find the lower bound among the sorted
+//    prefixes; only when the prefix at that position equals the query's does
+//    a second search find the end of the equal run, inside which lane 0
+//    refines the position by full keys (computed on demand from the planes).
+//  * Score: the window's candidates go 32 at a time. Every lane reads its 4
+//    coordinates of each candidate row (a row is read by the warp in 512-byte
+//    coalesced pieces) and keeps one partial sum per candidate; a transposing
+//    butterfly (31 shuffles) leaves candidate j's distance in lane j. The
+//    butterfly adds lane partials in the same tree for every candidate, so a
+//    (query, point) pair gets the same value in every tree.
+//  * Merge: the 32 scored candidates are sorted across the warp and inserted
+//    in ascending order until the first one that cannot enter.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -25,11 +33,12 @@
 namespace {
 
 constexpr int SWARPS = 4;
+constexpr unsigned FULL = 0xffffffffu;
 
-// Shared bytes per warp: list (k floats + k ids), query prefix (K words), two
-// coordinate scratch rows (d bytes each), rounded to 16.
-__host__ __device__ __forceinline__ size_t search_per_warp(int k, int K, int d) {
-  return ((size_t)k * 8 + (size_t)K * 8 + 2 * (size_t)d + 15) & ~(size_t)15;
+// Shared bytes per warp: query prefix (K words), candidate ids (32 words),
+// two coordinate scratch rows (d bytes each), rounded to 16.
+__host__ __device__ __forceinline__ size_t search_per_warp(int K, int d) {
+  return ((size_t)K * 8 + 32 * 4 + 2 * (size_t)d + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ bool lessp(float da, uint32_t ia, float db, uint32_t ib) {
@@ -55,6 +64,17 @@ __device__ __forceinline__ bool full_key_less(const uint8_t* Yd, const uint8_t* 
   return false;
 }
 
+// Running XOR from the most significant bit down: bit j of the result is the
+// XOR of bits 31..j of v.
+__device__ __forceinline__ uint32_t xor_scan_msb(uint32_t v) {
+  v ^= v >> 1;
+  v ^= v >> 2;
+  v ^= v >> 4;
+  v ^= v >> 8;
+  v ^= v >> 16;
+  return v;
+}
+
 struct SearchArgs {
   const float* x;
   int64_t n;
@@ -73,33 +93,39 @@ struct SearchArgs {
   int64_t* out_pos;
   int only_tree;
   int vec4;  // d % 4 == 0 and both matrices 16-byte aligned
-  const uint64_t* qkeys;  // [nq][T][K] query key prefixes, or null: computed in the search kernel
+  int top;   // the K prefix words lie in the top bit level (d >= 64K)
 };
 
-// Key prefixes of every (query, tree) pair, one thread each, so the search
-// kernel's lanes do not wait on a serial transform.
-__global__ void query_keys_kernel(const uint8_t* __restrict__ qcodes, int64_t nq, int d, int bits, int K, int L,
-                                  int T, int W32, const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
-                                  uint64_t* __restrict__ out) {
-  extern __shared__ uint8_t smy[];
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nq * T) return;
-  const int64_t qi = e / T;
-  const int t = (int)(e - qi * T);
-  uint8_t* Y = smy + (size_t)threadIdx.x * d;
-  hf_load_coords_codes(qcodes + (size_t)qi * d, d, bits, L, pi + (size_t)t * d, rbits + (size_t)t * W32, Y);
-  hf_skilling(Y, d, L);
-  for (int w = 0; w < K; ++w) out[(size_t)e * K + w] = hf_pack_word(Y, d, L, w);
+// Query prefix from the top bits, the warp taking 32 coordinates per ballot:
+// key bit i (i < 64K) is the XOR of the permuted, reflected top bits of
+// coordinates 0..i; word w holds bits 64w .. 64w+63, most significant first.
+__device__ __forceinline__ void warp_top_prefix(const uint8_t* __restrict__ qc, int bits, int K,
+                                                const int32_t* __restrict__ pi, const uint32_t* __restrict__ rb,
+                                                uint64_t* qp, int lane) {
+  uint32_t carry = 0;
+  for (int w = 0; w < K; ++w) {
+    uint32_t half[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = w * 64 + h * 32 + lane;
+      const uint32_t bit = (((uint32_t)qc[__ldg(pi + i)] >> (bits - 1)) ^ (__ldg(rb + (i >> 5)) >> lane)) & 1u;
+      uint32_t v = xor_scan_msb(__brev(__ballot_sync(FULL, bit)));
+      if (carry) v = ~v;
+      carry = v & 1u;
+      half[h] = v;
+    }
+    if (lane == 0) qp[w] = ((uint64_t)half[0] << 32) | half[1];
+  }
 }
 
-// Warp-wide lower bound over the sorted prefixes: each round the 32 lanes
-// probe 32 evenly spaced positions of [lo, hi) (one round trip), a ballot
-// keeps the sub-interval that holds the first position whose prefix is not
-// below the query's (le = false) or above it (le = true). About log32(n)
+// Warp-wide bound over the sorted prefixes in [lo, n): each round the 32
+// lanes probe 32 evenly spaced positions of [lo, hi) (one round trip), a
+// ballot keeps the sub-interval that holds the first position whose prefix is
+// not below the query's (le = false) or above it (le = true). About log32(n)
 // rounds instead of log2(n) dependent steps.
 __device__ __forceinline__ int64_t warp_bound(const uint64_t* __restrict__ pre, int64_t n, int K, const uint64_t* qp,
-                                              bool le, int lane) {
-  int64_t lo = 0, hi = n;  // answer in [lo, hi]
+                                              bool le, int64_t lo, int lane) {
+  int64_t hi = n;  // answer in [lo, hi]
   while (hi - lo > 0) {
     const int64_t len = hi - lo;
     const int64_t step = (len + 31) / 32;
@@ -109,7 +135,7 @@ __device__ __forceinline__ int64_t warp_bound(const uint64_t* __restrict__ pre, 
       const int c = cmp_prefix(pre, n, K, m, qp);
       below = le ? (c <= 0) : (c < 0);
     }
-    const uint32_t bm = __ballot_sync(0xffffffffu, below);
+    const uint32_t bm = __ballot_sync(FULL, below);
     const int cnt = __popc(bm);  // lanes 0 .. cnt-1 are below (monotone)
     if (cnt == 0) {
       hi = lo;
@@ -130,8 +156,8 @@ __device__ __forceinline__ void warp_sort(float& dv, uint32_t& iv, int lane) {
   for (int kk = 2; kk <= 32; kk <<= 1) {
 #pragma unroll
     for (int j = kk >> 1; j > 0; j >>= 1) {
-      const float od = __shfl_xor_sync(0xffffffffu, dv, j);
-      const uint32_t oi = __shfl_xor_sync(0xffffffffu, iv, j);
+      const float od = __shfl_xor_sync(FULL, dv, j);
+      const uint32_t oi = __shfl_xor_sync(FULL, iv, j);
       const bool up = (lane & kk) == 0;
       const bool lower = (lane & j) == 0;
       const bool other_less = lessp(od, oi, dv, iv);
@@ -144,15 +170,102 @@ __device__ __forceinline__ void warp_sort(float& dv, uint32_t& iv, int lane) {
   }
 }
 
+// Transposing butterfly: lane l holds v[u] = its partial for candidate u;
+// afterwards v[0] of lane l is the sum over all lanes of the partials for
+// candidate l. Step s pairs lanes l and l ^ s; the lane whose bit s is set
+// keeps the upper half of the remaining candidates.
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(FULL, send, s);
+    }
+  }
+  return v[0];
+}
+
+// Top-k list held across the warp: entry e = 32 s + lane in slot s.
+template <int S>
+struct WarpList {
+  float dv[S];
+  uint32_t iv[S];
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      dv[s] = INFINITY;
+      iv[s] = 0xffffffffu;
+    }
+  }
+  // Entry k - 1 (the one a candidate must beat).
+  __device__ __forceinline__ void last(int k, float& d, uint32_t& i) const {
+    const int s = (k - 1) >> 5, l = (k - 1) & 31;
+    float ds = dv[0];
+    uint32_t is = iv[0];
+#pragma unroll
+    for (int t = 1; t < S; ++t)
+      if (s == t) {
+        ds = dv[t];
+        is = iv[t];
+      }
+    d = __shfl_sync(FULL, ds, l);
+    i = __shfl_sync(FULL, is, l);
+  }
+  // Inserts (cd, ci) unless ci is already listed; entries at or beyond k are
+  // scratch.
+  __device__ __forceinline__ void insert(float cd, uint32_t ci, int k, int lane) {
+    bool dup = false;
+    int pos = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const bool valid = 32 * s + lane < k;
+      dup |= __ballot_sync(FULL, valid && iv[s] == ci) != 0;
+      pos += __popc(__ballot_sync(FULL, valid && lessp(dv[s], iv[s], cd, ci)));
+    }
+    if (dup) return;
+    float cd_prev[S];
+    uint32_t ci_prev[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      // entry e - 1: lane - 1 of the same slot, or lane 31 of the slot below
+      float up_d = __shfl_up_sync(FULL, dv[s], 1);
+      uint32_t up_i = __shfl_up_sync(FULL, iv[s], 1);
+      const float wrap_d = __shfl_sync(FULL, dv[s > 0 ? s - 1 : 0], 31);
+      const uint32_t wrap_i = __shfl_sync(FULL, iv[s > 0 ? s - 1 : 0], 31);
+      if (lane == 0) {
+        up_d = wrap_d;
+        up_i = wrap_i;
+      }
+      cd_prev[s] = up_d;
+      ci_prev[s] = up_i;
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int e = 32 * s + lane;
+      if (e > pos) {
+        dv[s] = cd_prev[s];
+        iv[s] = ci_prev[s];
+      } else if (e == pos) {
+        dv[s] = cd;
+        iv[s] = ci;
+      }
+    }
+  }
+};
+
+template <int S>
 __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const size_t per_warp = search_per_warp(a.k, a.K, a.d);
+  const size_t per_warp = search_per_warp(a.K, a.d);
   unsigned char* base = smraw + per_warp * wib;
-  float* ldst = reinterpret_cast<float*>(base);
-  uint32_t* lidx = reinterpret_cast<uint32_t*>(ldst + a.k);
-  uint64_t* qp = reinterpret_cast<uint64_t*>(lidx + a.k);  // 8k bytes in: 8-byte aligned
-  uint8_t* Yq = reinterpret_cast<uint8_t*>(qp + a.K);
+  uint64_t* qp = reinterpret_cast<uint64_t*>(base);
+  uint32_t* cpid = reinterpret_cast<uint32_t*>(qp + a.K);
+  uint8_t* Yq = reinterpret_cast<uint8_t*>(cpid + 32);
   uint8_t* Yd = Yq + a.d;
 
   const int64_t qi = (int64_t)blockIdx.x * SWARPS + wib;
@@ -160,11 +273,8 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
   const uint8_t* qc = a.qcodes + (size_t)qi * a.d;
   const float* qv = a.q + (size_t)qi * a.d;
 
-  for (int j = lane; j < a.k; j += 32) {
-    ldst[j] = INFINITY;
-    lidx[j] = 0xffffffffu;
-  }
-  __syncwarp();
+  WarpList<S> list;
+  list.init();
 
   const int t_begin = a.only_tree >= 0 ? a.only_tree : 0;
   const int t_end = a.only_tree >= 0 ? a.only_tree + 1 : a.T;
@@ -173,19 +283,19 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
     const uint32_t* rb = a.rbits + (size_t)t * a.W32;
     const uint64_t* pre = a.prefix + (size_t)t * a.K * a.n;
     const uint32_t* sig = a.sigma + (size_t)t * a.n;
-    if (a.qkeys) {
-      if (lane < a.K) qp[lane] = __ldg(a.qkeys + ((size_t)qi * a.T + t) * a.K + lane);
+    if (a.top) {
+      warp_top_prefix(qc, a.bits, a.K, pi, rb, qp, lane);
     } else if (lane == 0) {
       hf_load_coords_codes(qc, a.d, a.bits, a.L, pi, rb, Yq);
       hf_skilling(Yq, a.d, a.L);
       for (int w = 0; w < a.K; ++w) qp[w] = hf_pack_word(Yq, a.d, a.L, w);
     }
     __syncwarp();
-    // [lo, lo2): positions whose prefix equals the query's
-    int64_t lo = warp_bound(pre, a.n, a.K, qp, false, lane);
-    const int64_t lo2 = warp_bound(pre, a.n, a.K, qp, true, lane);
+    const int64_t lo = warp_bound(pre, a.n, a.K, qp, false, 0, lane);
     int64_t pos = lo;
-    if (lo2 > lo && a.K < a.W) {
+    // [lo, lo2): positions whose prefix equals the query's
+    if (a.K < a.W && lo < a.n && cmp_prefix(pre, a.n, a.K, lo, qp) == 0) {
+      const int64_t lo2 = warp_bound(pre, a.n, a.K, qp, true, lo, lane);
       if (lane == 0) {
         // equal prefixes: lower bound by full key inside [lo, lo2)
         hf_load_coords_codes(qc, a.d, a.bits, a.bits, pi, rb, Yq);
@@ -200,7 +310,7 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
         }
         pos = l;
       }
-      pos = __shfl_sync(0xffffffffu, pos, 0);
+      pos = __shfl_sync(FULL, pos, 0);
     }
     if (a.only_tree >= 0) {
       if (lane == 0) a.out_pos[qi] = pos;
@@ -209,86 +319,89 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
     const int64_t c0 = pos - a.w > 0 ? pos - a.w : 0;
     const int64_t c1 = pos + a.w < a.n ? pos + a.w : a.n;
     for (int64_t cb = c0; cb < c1; cb += 32) {
-      // lane j scores candidate cb + j over the whole vector
       const int64_t c = cb + lane;
-      float dist = INFINITY;
-      uint32_t pid = 0xffffffffu;
-      if (c < c1) {
-        pid = __ldg(sig + c);
-        const float* xv = a.x + (size_t)pid * a.d;
-        float acc = 0.f;
-        if (a.vec4) {
-          for (int j = 0; j < a.d; j += 4) {
-            const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + j));
-            const float4 xa = __ldg(reinterpret_cast<const float4*>(xv + j));
-            float e = qa.x - xa.x;
-            acc = fmaf(e, e, acc);
-            e = qa.y - xa.y;
-            acc = fmaf(e, e, acc);
-            e = qa.z - xa.z;
-            acc = fmaf(e, e, acc);
-            e = qa.w - xa.w;
-            acc = fmaf(e, e, acc);
-          }
-        } else {
-          for (int j = 0; j < a.d; ++j) {
-            const float e = __ldg(qv + j) - __ldg(xv + j);
-            acc = fmaf(e, e, acc);
+      uint32_t pid = c < c1 ? __ldg(sig + c) : 0xffffffffu;
+      float dist;
+      if (a.vec4) {
+        cpid[lane] = pid;
+        __syncwarp();
+        float part[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) part[u] = 0.f;
+        for (int m = 4 * lane; m < a.d; m += 128) {
+          const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + m));
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            const uint32_t p = cpid[u];
+            if (p != 0xffffffffu) {
+              const float4 xa = __ldg(reinterpret_cast<const float4*>(a.x + (size_t)p * a.d + m));
+              float e = qa.x - xa.x;
+              float acc = fmaf(e, e, part[u]);
+              e = qa.y - xa.y;
+              acc = fmaf(e, e, acc);
+              e = qa.z - xa.z;
+              acc = fmaf(e, e, acc);
+              e = qa.w - xa.w;
+              part[u] = fmaf(e, e, acc);
+            }
           }
         }
-        dist = acc;
+        dist = warp_transpose_sum(part, lane);
+        __syncwarp();
+      } else {
+        // one lane per candidate over the whole vector
+        dist = 0.f;
+        if (pid != 0xffffffffu) {
+          const float* xv = a.x + (size_t)pid * a.d;
+          for (int j = 0; j < a.d; ++j) {
+            const float e = __ldg(qv + j) - __ldg(xv + j);
+            dist = fmaf(e, e, dist);
+          }
+        }
       }
+      if (pid == 0xffffffffu) dist = INFINITY;
       warp_sort(dist, pid, lane);
       // merge in ascending order; stop at the first that cannot enter
       for (int u = 0; u < 32; ++u) {
-        const float cd = __shfl_sync(0xffffffffu, dist, u);
-        const uint32_t ci = __shfl_sync(0xffffffffu, pid, u);
+        const float cd = __shfl_sync(FULL, dist, u);
+        const uint32_t ci = __shfl_sync(FULL, pid, u);
         if (ci == 0xffffffffu) break;
-        if (!lessp(cd, ci, ldst[a.k - 1], lidx[a.k - 1])) break;
-        if (lane == 0) {
-          bool dup = false;
-          for (int j = 0; j < a.k; ++j) dup |= (lidx[j] == ci);
-          if (!dup) {
-            int j = a.k - 1;
-            while (j > 0 && lessp(cd, ci, ldst[j - 1], lidx[j - 1])) {
-              ldst[j] = ldst[j - 1];
-              lidx[j] = lidx[j - 1];
-              --j;
-            }
-            ldst[j] = cd;
-            lidx[j] = ci;
-          }
-        }
-        __syncwarp();
+        float kd;
+        uint32_t ki;
+        list.last(a.k, kd, ki);
+        if (!lessp(cd, ci, kd, ki)) break;
+        list.insert(cd, ci, a.k, lane);
       }
     }
   }
   if (a.only_tree >= 0) return;
-  __syncwarp();
-  for (int j = lane; j < a.k; j += 32) {
-    a.out_idx[(size_t)qi * a.k + j] = lidx[j];
-    a.out_dist[(size_t)qi * a.k + j] = ldst[j];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = 32 * s + lane;
+    if (e < a.k) {
+      a.out_idx[(size_t)qi * a.k + e] = list.iv[s];
+      a.out_dist[(size_t)qi * a.k + e] = list.dv[s];
+    }
   }
+}
+
+template <int S>
+int launch_s(const SearchArgs& a, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute((const void*)search_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return HF_ECUDA;
+  search_kernel<S><<<hf_blocks(a.nq, SWARPS), SWARPS * 32, smem, s>>>(a);
+  hf_after_launch("search_kernel", s);
+  return HF_OK;
 }
 
 }  // namespace
 
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k, int w,
-                  uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree, cudaStream_t s,
-                  uint64_t* qkeys) {
+                  uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree, cudaStream_t s) {
+  if (k < 1 || k > 64) return HF_EINVAL;
   SearchArgs a;
-  a.qkeys = nullptr;
-  if (qkeys && only_tree < 0) {
-    int t = 256;
-    while (t > 32 && (size_t)t * f->d > 96 * 1024) t >>= 1;
-    const size_t sm = (size_t)t * f->d;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute((const void*)query_keys_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    query_keys_kernel<<<hf_blocks(nq * f->T, t), t, sm, s>>>(qcodes, nq, f->d, f->bits, f->K, f->L, f->T, f->W32,
-                                                               f->pi, f->rbits, qkeys);
-    hf_after_launch("query_keys_kernel", s);
-    a.qkeys = qkeys;
-  }
   a.x = f->x;
   a.n = f->n;
   a.d = f->d;
@@ -314,12 +427,10 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
   a.only_tree = only_tree;
   a.vec4 = (f->d % 4 == 0) && ((reinterpret_cast<uintptr_t>(f->x) & 15) == 0) &&
            ((reinterpret_cast<uintptr_t>(q) & 15) == 0);
-  const size_t smem = search_per_warp(k, f->K, f->d) * SWARPS;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute((const void*)search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-    return HF_ECUDA;
-  search_kernel<<<hf_blocks(nq, SWARPS), SWARPS * 32, smem, s>>>(a); hf_after_launch("search_kernel", s);
+  a.top = f->d >= 64 * f->K;
+  const size_t smem = search_per_warp(f->K, f->d) * SWARPS;
+  const int rc = k <= 32 ? launch_s<1>(a, smem, s) : launch_s<2>(a, smem, s);
+  if (rc != HF_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
 
