@@ -247,10 +247,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   const int N = a.N, nk = a.dp / KC;
   const size_t stage_bytes = (size_t)N * 128;
-  uint32_t* mrow = reinterpret_cast<uint32_t*>(base + STAGES * stage_bytes);  // [2][N] row ids
-  float* mnorm = reinterpret_cast<float*>(mrow + 2 * N);                      // [2][N] norms
-  float* cbd = mnorm + 2 * N;                                                 // [32][256]
-  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);                // [32][256]
+  const int NP = N + 32;  // padded: an epilogue chunk may run past column N - 1
+  float2* mnid = reinterpret_cast<float2*>(base + STAGES * stage_bytes);  // [2][NP] (norm, id bits)
+  float* cbd = reinterpret_cast<float*>(mnid + 2 * NP);                   // [32][256]
+  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);            // [32][256]
   PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 256 * 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -286,18 +286,33 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
-      uint32_t* srow = mrow + buf * N;
-      float* snorm = mnorm + buf * N;
+      float2* snid = mnid + buf * NP;
       const int64_t r0 = t * GB - a.W8;
-      for (int r = lt; r < N; r += LW * 32) {
+      for (int r = lt; r < NP; r += LW * 32) {
         const int64_t p = r0 + r;
-        const bool okr = p >= 0 && p < a.n;
+        const bool okr = r < N && p >= 0 && p < a.n;
         const uint32_t pid = okr ? __ldg(a.sigma + p) : 0xffffffffu;
-        srow[r] = pid;
-        snorm[r] = okr ? __ldg(a.nrm + pid) : 0.f;
+        // rows outside the matrix get a NaN norm: their distances never pass a screen
+        snid[r] = make_float2(okr ? __ldg(a.nrm + pid) : __uint_as_float(0x7fc00000u), __uint_as_float(pid));
       }
       asm volatile("bar.sync 1, %0;" ::"r"(LW * 32) : "memory");  // loaders only
       if (lt == 0) mbar_arrive(&S.mfull[buf]);
+      // this thread's pieces: the same (row, 16-byte column) in every chunk,
+      // so sources and swizzled destinations are formed once per tile
+      constexpr int PER = 16;
+      const __nv_bfloat16* src[PER];
+      uint32_t dsto[PER];
+      uint32_t lmask = 0, smask = 0;  // pieces to load / to store
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = lt + q * LW * 32;
+        const int r = e >> 3, j = e & 7;
+        const uint32_t pid = e < N * 8 ? __float_as_uint(snid[r].y) : 0xffffffffu;
+        src[q] = a.xb + (pid != 0xffffffffu ? (size_t)pid * a.dp : 0) + j * 8;
+        dsto[q] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+        if (e < N * 8) smask |= 1u << q;
+        if (pid != 0xffffffffu) lmask |= 1u << q;
+      }
       bool ok = true;
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const int st = it % STAGES;
@@ -306,27 +321,15 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
           break;
         }
         unsigned char* dst0 = base + st * stage_bytes;
-        // N * 8 16-byte pieces; up to 16 per thread, all loads issued first
-        constexpr int PER = 16;
         uint4 v[PER];
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-          const int e = lt + q * LW * 32;
           v[q] = make_uint4(0, 0, 0, 0);
-          if (e < N * 8) {
-            const uint32_t pid = srow[e >> 3];
-            if (pid != 0xffffffffu)
-              v[q] = __ldg(reinterpret_cast<const uint4*>(a.xb + (size_t)pid * a.dp + kc * KC) + (e & 7));
-          }
+          if ((lmask >> q) & 1u) v[q] = __ldg(reinterpret_cast<const uint4*>(src[q] + kc * KC));
         }
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int e = lt + q * LW * 32;
-          if (e < N * 8) {
-            const int r = e >> 3, j = e & 7;
-            *reinterpret_cast<uint4*>(dst0 + (r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4)) = v[q];
-          }
-        }
+        for (int q = 0; q < PER; ++q)
+          if ((smask >> q) & 1u) *reinterpret_cast<uint4*>(dst0 + dsto[q]) = v[q];
         fence_proxy_async_smem();  // these stores, seen by the tensor core
         mbar_arrive(&S.full[st]);
       }
@@ -380,34 +383,36 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
       if (!pwait(&S.mfull[buf], use & 1, lim, abort, a.err)) break;
       if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
       tc_fence_after();
-      const uint32_t* srow = mrow + buf * N;
-      const float* snorm = mnorm + buf * N;
+      const float2* snid = mnid + buf * NP;
       const int64_t p = t * GB + r;
       const bool rowok = p < a.n;
       ListK<KP> L;
-      uint32_t ip = 0;
-      if (rowok) {
-        ip = srow[r + a.W8];
-        L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
-      }
-      const float np_ = snorm[r + a.W8];
+      const float2 own = snid[r + a.W8];
+      const uint32_t ip = __float_as_uint(own.y);
+      if (rowok) L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+      const float np_ = own.x;
+      // the row's band: columns [r + W8 - w, r + W8 + w] except r + W8 itself
+      const int wlo = r + a.W8 - a.w, whi = r + a.W8 + a.w, diag = r + a.W8;
       const int cfirst = 32 * quarter;
       const int clast = 32 * quarter + 31 + 2 * a.W8;
       for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(tmem + (uint32_t)(buf * 256) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+        const int lo = wlo - c0 > 0 ? wlo - c0 : 0;
+        const int hi = whi - c0 < 31 ? whi - c0 : 31;
+        uint32_t wm = 0;
+        if (rowok && lo <= hi) wm = (0xffffffffu >> (31 - hi + lo)) << lo;
+        if (diag >= c0 && diag < c0 + 32) wm &= ~(1u << (diag - c0));
+        // screen against the current last entry (ties pass; the offer decides)
         const float td = L.d[KP - 1];
-        const uint32_t ti = L.i[KP - 1];
         int m = 0;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
-          const int c = c0 + jj;
-          const int delta = c - a.W8 - r;
-          const uint32_t q = c < N ? srow[c] : 0xffffffffu;
-          const float d2 = np_ + (c < N ? snorm[c] : 0.f) - 2.0f * __uint_as_float(v[jj]);
-          if (rowok && delta != 0 && delta >= -a.w && delta <= a.w && q != 0xffffffffu && lessp(d2, q, td, ti)) {
+          const float2 e = snid[c0 + jj];
+          const float d2 = np_ + e.x - 2.0f * __uint_as_float(v[jj]);
+          if (((wm >> jj) & 1u) && d2 <= td) {
             mybd[m * 256] = d2;
-            mybi[m * 256] = q;
+            mybi[m * 256] = __float_as_uint(e.y);
             ++m;
           }
         }
@@ -435,56 +440,96 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   }
 }
 
+// Transposing butterfly over NV candidates (NV = 16 or 32): lane l holds
+// v[u] = its partial sum for candidate u; afterwards the return value of lane
+// l is the total over all lanes for candidate l % NV.
+template <int NV>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[NV], int lane) {
+#pragma unroll
+  for (int s = NV / 2; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  float r = v[0];
+#pragma unroll
+  for (int o = NV; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
 // Exact re-rank: one warp per point, points taken in the order of the first
-// tree (consecutive warps then share most candidate rows in L2). The lanes
-// split the coordinates (coalesced row reads) and score 8 listed candidates
-// at a time with float32 exact differences; a butterfly sum per candidate
-// gives its distance. The KP entries are then re-sorted by (distance, index);
+// tree (consecutive warps then share most candidate rows in L2). Listed
+// candidates are scored up to 32 at a time with float32 exact differences:
+// every lane reads its coordinates of each candidate row (the warp reads a row
+// in coalesced 512-byte pieces when rows are float4-aligned) and keeps one
+// partial sum per candidate; a transposing butterfly gives candidate j's
+// distance in lane j. The KP entries are then re-sorted by (distance, index);
 // empty slots stay (+inf, 0xffffffff).
 template <int KP>
 __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x, int64_t n, int d,
-                                                     const uint32_t* __restrict__ order,
+                                                     const uint32_t* __restrict__ order, int vec4,
                                                      uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   constexpr int PER = (KP + 31) / 32;
-  constexpr int G = 8;
-  const int lane = threadIdx.x & 31;
+  constexpr int NV = KP < 32 ? KP : 32;  // candidates per round
+  __shared__ uint32_t s_c[256 / 32][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (wi >= n) return;
   const int64_t i = order ? (int64_t)__ldg(order + wi) : wi;
   const float* xi = x + (size_t)i * d;
-  const uint32_t mine = lane < KP ? lidx[(size_t)i * KP + lane] : 0xffffffffu;
-  const uint32_t mine2 = (PER > 1 && lane + 32 < KP) ? lidx[(size_t)i * KP + lane + 32] : 0xffffffffu;
   float dd[PER];
   uint32_t id[PER];
-  id[0] = mine;
-  if (PER > 1) id[PER - 1] = mine2;
 #pragma unroll
-  for (int u = 0; u < PER; ++u) dd[u] = INFINITY;
-  for (int g0 = 0; g0 < KP; g0 += G) {
-    uint32_t c[G];
-    float acc[G];
+  for (int u = 0; u < PER; ++u) {
+    id[u] = 32 * u + lane < KP ? lidx[(size_t)i * KP + 32 * u + lane] : 0xffffffffu;
+    dd[u] = INFINITY;
+  }
 #pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int slot = g0 + t;
-      c[t] = __shfl_sync(0xffffffffu, slot < 32 ? mine : mine2, slot & 31);
-      acc[t] = 0.f;
-    }
-    for (int j = lane; j < d; j += 32) {
-      const float xv = __ldg(xi + j);
+  for (int g = 0; g < PER; ++g) {
+    s_c[wib][lane] = id[g];
+    __syncwarp();
+    float part[NV];
 #pragma unroll
-      for (int t = 0; t < G; ++t)
-        if (c[t] != 0xffffffffu) {
-          const float e = xv - __ldg(x + (size_t)c[t] * d + j);
-          acc[t] = fmaf(e, e, acc[t]);
+    for (int u = 0; u < NV; ++u) part[u] = 0.f;
+    if (vec4) {
+      for (int m = 4 * lane; m < d; m += 128) {
+        const float4 xa = __ldg(reinterpret_cast<const float4*>(xi + m));
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+          const uint32_t c = s_c[wib][u];
+          if (c != 0xffffffffu) {
+            const float4 xb = __ldg(reinterpret_cast<const float4*>(x + (size_t)c * d + m));
+            float e = xa.x - xb.x;
+            float acc = fmaf(e, e, part[u]);
+            e = xa.y - xb.y;
+            acc = fmaf(e, e, acc);
+            e = xa.z - xb.z;
+            acc = fmaf(e, e, acc);
+            e = xa.w - xb.w;
+            part[u] = fmaf(e, e, acc);
+          }
         }
-    }
+      }
+    } else {
+      for (int m = lane; m < d; m += 32) {
+        const float xa = __ldg(xi + m);
 #pragma unroll
-    for (int t = 0; t < G; ++t) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-      const int slot = g0 + t;
-      if (c[t] != 0xffffffffu && (slot & 31) == lane) dd[slot >> 5] = acc[t];
+        for (int u = 0; u < NV; ++u) {
+          const uint32_t c = s_c[wib][u];
+          if (c != 0xffffffffu) {
+            const float e = xa - __ldg(x + (size_t)c * d + m);
+            part[u] = fmaf(e, e, part[u]);
+          }
+        }
+      }
     }
+    const float dist = warp_transpose_sum<NV>(part, lane);
+    if (id[g] != 0xffffffffu) dd[g] = dist;
+    __syncwarp();
   }
   // rank of each lane's entries among all KP entries by (distance, index,
   // slot): unique even among empty slots; padding slots (>= KP) rank last
@@ -510,7 +555,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x
 
 size_t gram_smem(int N, int dp) {
   (void)dp;
-  return (size_t)STAGES * N * 128 + (size_t)2 * N * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
+  return (size_t)STAGES * N * 128 + (size_t)2 * (N + 32) * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
 }
 
 template <int KP>
@@ -609,10 +654,11 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
 int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
                   cudaStream_t s) {
   const unsigned blocks = hf_blocks(n * 32, 256);
+  const int vec4 = d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   switch (kp) {
-    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
-    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
-    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, order, li, ld); break;
+    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
+    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
+    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
     default: return HF_EINVAL;
   }
   hf_after_launch("rerank_kernel", s);
