@@ -121,9 +121,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return desc;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  const int sz = valid ? 16 : 0;  // 0: zero fill
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(sz) : "memory");
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// 16-byte asynchronous copy global -> shared (zero fill when !valid).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // BF16 copy of the points (row pitch dp, a multiple of 64, zero padded) and
@@ -165,9 +175,9 @@ struct GramArgs {
 // Persistent, warp-specialised Gram kernel. One block per SM loops over tiles
 // (tile t = blockIdx.x + i * gridDim.x). Warps 0..3 (loaders) write the
 // tile's row ids and norms and gather its rows into a ring of STAGES K-chunk
-// buffers: 16-byte global loads into registers (many in flight per thread),
-// then stores into the swizzled layout, a proxy fence, and one arrival per
-// thread on the chunk's "full" barrier. Warp 4 (MMA) issues the chunk's four
+// buffers with 16-byte asynchronous copies into the swizzled layout; each
+// thread keeps DEPTH chunks in flight and, once the oldest has landed, issues
+// a proxy fence and its arrival on that chunk's "full" barrier. Warp 4 (MMA) issues the chunk's four
 // K = 16 MMAs into one of two tensor-memory accumulators and releases the
 // chunk buffer through tcgen05.commit. Warps 5..8 and 9..12 form two epilogue
 // groups that take alternate tiles (one accumulator each): each thread owns
@@ -178,6 +188,8 @@ struct GramArgs {
 // bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
 constexpr int STAGES = 4;
+constexpr int DEPTH = 3;           // K chunks a loader keeps in flight (< STAGES)
+constexpr int PER = 16;            // 16-byte pieces per loader thread and chunk
 constexpr int LW = 4;              // loader warps (warps 0..3)
 constexpr int MW = LW;             // MMA warp
 constexpr int EW0 = LW + 1;        // first epilogue warp (two groups of 4)
@@ -281,25 +293,46 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     // ---------------- loaders: 128 threads
     const int lt = tid;  // 0 .. 127
     uint32_t it = 0;     // chunk counter across tiles
+    int pending = 0;     // chunks issued but not yet marked full
     int tl = 0;
+    // Row ids (and then norms) of the next tile are loaded into registers
+    // while the current tile streams, so a tile starts without a dependent
+    // pair of global round trips. Thread lt stages rows lt + 128 j.
+    constexpr int RPT = 3;  // ceil((N + 32) / 128) for N <= 256
+    uint32_t npid[RPT];
+    float nnrm[RPT];
+    auto fetch_ids = [&](int64_t tt) {
+      const int64_t rr0 = tt * GB - a.W8;
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        const int r = lt + j * LW * 32;
+        const int64_t p = rr0 + r;
+        npid[j] = (tt < ntiles && r < N && p >= 0 && p < a.n) ? __ldg(a.sigma + p) : 0xffffffffu;
+      }
+    };
+    auto fetch_norms = [&]() {
+#pragma unroll
+      for (int j = 0; j < RPT; ++j)
+        nnrm[j] = npid[j] != 0xffffffffu ? __ldg(a.nrm + npid[j]) : __uint_as_float(0x7fc00000u);
+    };
+    fetch_ids(blockIdx.x);
+    fetch_norms();
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
       float2* snid = mnid + buf * NP;
-      const int64_t r0 = t * GB - a.W8;
-      for (int r = lt; r < NP; r += LW * 32) {
-        const int64_t p = r0 + r;
-        const bool okr = r < N && p >= 0 && p < a.n;
-        const uint32_t pid = okr ? __ldg(a.sigma + p) : 0xffffffffu;
-        // rows outside the matrix get a NaN norm: their distances never pass a screen
-        snid[r] = make_float2(okr ? __ldg(a.nrm + pid) : __uint_as_float(0x7fc00000u), __uint_as_float(pid));
+      // rows outside the matrix get a NaN norm: their distances never pass a screen
+#pragma unroll
+      for (int j = 0; j < RPT; ++j) {
+        const int r = lt + j * LW * 32;
+        if (r < NP) snid[r] = make_float2(nnrm[j], __uint_as_float(npid[j]));
       }
+      fetch_ids(t + gridDim.x);
       asm volatile("bar.sync 1, %0;" ::"r"(LW * 32) : "memory");  // loaders only
       if (lt == 0) mbar_arrive(&S.mfull[buf]);
       // this thread's pieces: the same (row, 16-byte column) in every chunk,
       // so sources and swizzled destinations are formed once per tile
-      constexpr int PER = 16;
       const __nv_bfloat16* src[PER];
       uint32_t dsto[PER];
       uint32_t lmask = 0, smask = 0;  // pieces to load / to store
@@ -320,21 +353,34 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
           ok = false;
           break;
         }
-        unsigned char* dst0 = base + st * stage_bytes;
-        uint4 v[PER];
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          v[q] = make_uint4(0, 0, 0, 0);
-          if ((lmask >> q) & 1u) v[q] = __ldg(reinterpret_cast<const uint4*>(src[q] + kc * KC));
-        }
+        const uint32_t dst0 = smem_u32(base + st * stage_bytes);
 #pragma unroll
         for (int q = 0; q < PER; ++q)
-          if ((smask >> q) & 1u) *reinterpret_cast<uint4*>(dst0 + dsto[q]) = v[q];
-        fence_proxy_async_smem();  // these stores, seen by the tensor core
-        mbar_arrive(&S.full[st]);
+          if ((smask >> q) & 1u) cp_async16(dst0 + dsto[q], src[q] + kc * KC, (lmask >> q) & 1u);
+        cp_async_commit();
+        // keep DEPTH chunks in flight: once the oldest has landed, make its
+        // stores visible to the tensor core and mark its stage full
+        if (++pending == DEPTH) {
+          cp_async_wait<DEPTH - 1>();
+          fence_proxy_async_smem();
+          mbar_arrive(&S.full[(it - (DEPTH - 1)) % STAGES]);
+          --pending;
+        }
       }
+      fetch_norms();  // the next tile's ids have arrived by now
       if (!ok) break;
+      if (nk < DEPTH) {
+        // a later tile's accumulator wait must not depend on this tile's
+        // chunks still being held back
+        cp_async_wait<0>();
+        fence_proxy_async_smem();
+        for (; pending > 0; --pending) mbar_arrive(&S.full[(it - pending) % STAGES]);
+      }
     }
+    // the last chunks (also after an abort: no copy may be in flight at exit)
+    cp_async_wait<0>();
+    fence_proxy_async_smem();
+    for (; pending > 0; --pending) mbar_arrive(&S.full[(it - pending) % STAGES]);
   } else if (warp == MW) {
     // ---------------- MMA issuer (one lane)
     if (lane == 0) {
@@ -381,8 +427,7 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
          t += 2 * (int64_t)gridDim.x, tl += 2) {
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!pwait(&S.mfull[buf], use & 1, lim, abort, a.err)) break;
-      if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
-      tc_fence_after();
+      // the row's list is fetched while the tile's MMAs run
       const float2* snid = mnid + buf * NP;
       const int64_t p = t * GB + r;
       const bool rowok = p < a.n;
@@ -390,6 +435,8 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
       const float2 own = snid[r + a.W8];
       const uint32_t ip = __float_as_uint(own.y);
       if (rowok) L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+      if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
+      tc_fence_after();
       const float np_ = own.x;
       // the row's band: columns [r + W8 - w, r + W8 + w] except r + W8 itself
       const int wlo = r + a.W8 - a.w, whi = r + a.W8 + a.w, diag = r + a.W8;
