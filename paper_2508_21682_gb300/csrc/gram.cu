@@ -173,21 +173,24 @@ struct GramArgs {
 
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised Gram kernel. One block per SM loops over tiles
-// (tile t = blockIdx.x + i * gridDim.x). Warps 0..3 (loaders) write the
-// tile's row ids and norms and gather its rows into a ring of STAGES K-chunk
-// buffers with 16-byte asynchronous copies into the swizzled layout; each
-// thread keeps DEPTH chunks in flight and, once the oldest has landed, issues
-// a proxy fence and its arrival on that chunk's "full" barrier. Warp 4 (MMA) issues the chunk's four
-// K = 16 MMAs into one of two tensor-memory accumulators and releases the
-// chunk buffer through tcgen05.commit. Warps 5..8 and 9..12 form two epilogue
-// groups that take alternate tiles (one accumulator each): each thread owns
-// one row (tensor-memory lane), screens its band and merges into the point's
-// list.
+// (tile t = blockIdx.x + i * gridDim.x). Warps 0..3 (loaders) stage the
+// tile's row ids and norms in one of NSLOT slots (so they can run up to
+// NSLOT - 1 tiles ahead of the epilogue) and gather its rows into a ring of
+// STAGES K-chunk buffers with 16-byte asynchronous copies into the swizzled
+// layout; each thread keeps DEPTH chunks in flight and, once the oldest has
+// landed, issues a proxy fence and its arrival on that chunk's "full"
+// barrier. Warp 4 (MMA) issues the chunk's four K = 16 MMAs into one of two
+// tensor-memory accumulators and releases the chunk buffer through
+// tcgen05.commit. Warps 5..8 and 9..12 form two epilogue groups that take
+// alternate tiles (one accumulator each): each thread owns one row
+// (tensor-memory lane), screens its band and merges into the point's list,
+// then releases the accumulator and the staged slot.
 // Every wait on a barrier is bounded; when one gives up, the block raises the
 // error word, every role leaves its loop, and tensor memory is freed after a
 // bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
 constexpr int STAGES = 4;
+constexpr int NSLOT = 4;           // staged (norm, id) rows: tiles the loaders may run ahead
 constexpr int DEPTH = 3;           // K chunks a loader keeps in flight (< STAGES)
 constexpr int PER = 16;            // 16-byte pieces per loader thread and chunk
 constexpr int LW = 4;              // loader warps (warps 0..3)
@@ -220,7 +223,8 @@ __device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, i
 
 struct PersistSmem {
   uint64_t full[STAGES], empty[STAGES];
-  uint64_t tfull[2], tempty[2], mfull[2];
+  uint64_t tfull[2], tempty[2];
+  uint64_t mfull[NSLOT], mempty[NSLOT];
   uint32_t tslot;
   int abort;
 };
@@ -260,8 +264,8 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
   const int N = a.N, nk = a.dp / KC;
   const size_t stage_bytes = (size_t)N * 128;
   const int NP = N + 32;  // padded: an epilogue chunk may run past column N - 1
-  float2* mnid = reinterpret_cast<float2*>(base + STAGES * stage_bytes);  // [2][NP] (norm, id bits)
-  float* cbd = reinterpret_cast<float*>(mnid + 2 * NP);                   // [32][256]
+  float2* mnid = reinterpret_cast<float2*>(base + STAGES * stage_bytes);  // [NSLOT][NP] (norm, id bits)
+  float* cbd = reinterpret_cast<float*>(mnid + NSLOT * NP);               // [32][256]
   uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);            // [32][256]
   PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 256 * 32);
 
@@ -278,7 +282,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.tfull[i], 1);
       mbar_init(&S.tempty[i], 4);
+    }
+    for (int i = 0; i < NSLOT; ++i) {
       mbar_init(&S.mfull[i], 1);
+      mbar_init(&S.mempty[i], 4);
     }
     S.abort = 0;
     fence_mbar_init();
@@ -318,10 +325,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     fetch_ids(blockIdx.x);
     fetch_norms();
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
-      const int buf = tl & 1;
-      const uint32_t use = (uint32_t)(tl >> 1);
-      if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
-      float2* snid = mnid + buf * NP;
+      const int slot = tl % NSLOT;
+      const uint32_t suse = (uint32_t)(tl / NSLOT);
+      if (!pwait(&S.mempty[slot], (suse & 1) ^ 1, lim, abort, a.err)) break;
+      float2* snid = mnid + slot * NP;
       // rows outside the matrix get a NaN norm: their distances never pass a screen
 #pragma unroll
       for (int j = 0; j < RPT; ++j) {
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
       }
       fetch_ids(t + gridDim.x);
       asm volatile("bar.sync 1, %0;" ::"r"(LW * 32) : "memory");  // loaders only
-      if (lt == 0) mbar_arrive(&S.mfull[buf]);
+      if (lt == 0) mbar_arrive(&S.mfull[slot]);
       // this thread's pieces: the same (row, 16-byte column) in every chunk,
       // so sources and swizzled destinations are formed once per tile
       const __nv_bfloat16* src[PER];
@@ -426,9 +433,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
     for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles && !*abort;
          t += 2 * (int64_t)gridDim.x, tl += 2) {
       const uint32_t use = (uint32_t)(tl >> 1);
-      if (!pwait(&S.mfull[buf], use & 1, lim, abort, a.err)) break;
+      const int sl = tl % NSLOT;
+      if (!pwait(&S.mfull[sl], (tl / NSLOT) & 1, lim, abort, a.err)) break;
       // the row's list is fetched while the tile's MMAs run
-      const float2* snid = mnid + buf * NP;
+      const float2* snid = mnid + sl * NP;
       const int64_t p = t * GB + r;
       const bool rowok = p < a.n;
       ListK<KP> L;
@@ -469,7 +477,10 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __
       if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.tempty[buf]);
+      if (lane == 0) {
+        mbar_arrive(&S.tempty[buf]);
+        mbar_arrive(&S.mempty[sl]);
+      }
     }
   }
   // teardown: the last commit completes before tensor memory is freed
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x
 
 size_t gram_smem(int N, int dp) {
   (void)dp;
-  return (size_t)STAGES * N * 128 + (size_t)2 * (N + 32) * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
+  return (size_t)STAGES * N * 128 + (size_t)NSLOT * (N + 32) * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
 }
 
 template <int KP>
