@@ -61,22 +61,40 @@ __global__ void range_partial_kernel(const float* __restrict__ x, int64_t total_
   }
 }
 
-// Column c of the result reduces partials of threads t with (t*VEC) % d == c - v.
+// One block per column c: the partials of threads t with (t*VEC) % d == c - v
+// are reduced by the block's threads, then across the block.
 __global__ void range_final_kernel(const float* __restrict__ pmin, const float* __restrict__ pmax,
                                    int64_t nthreads, int vec, int d, int bits,
                                    float* __restrict__ lo, float* __restrict__ scale) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= d) return;
+  __shared__ float smn[32], smx[32];
+  const int c = blockIdx.x;
   const int groups = d / vec;  // threads per "row" of column groups
   const int g = c / vec, v = c % vec;
   float mn = INFINITY, mx = -INFINITY;
-  for (int64_t t = g; t < nthreads; t += groups) {
+  for (int64_t t = g + (int64_t)threadIdx.x * groups; t < nthreads; t += (int64_t)blockDim.x * groups) {
     mn = fminf(mn, pmin[t * vec + v]);
     mx = fmaxf(mx, pmax[t * vec + v]);
   }
-  lo[c] = mn;
-  const float width = __fsub_rn(mx, mn);
-  scale[c] = width > 0.0f ? (float)((double)(1u << bits) / (double)width) : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    smn[wid] = mn;
+    smx[wid] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mn = fminf(mn, smn[w]);
+      mx = fmaxf(mx, smx[w]);
+    }
+    lo[c] = mn;
+    const float width = __fsub_rn(mx, mn);
+    scale[c] = width > 0.0f ? (float)((double)(1u << bits) / (double)width) : 0.0f;
+  }
 }
 
 __device__ __forceinline__ uint32_t quantize_one(float x, float lo, float scale, int bits) {
@@ -88,29 +106,55 @@ __device__ __forceinline__ uint32_t quantize_one(float x, float lo, float scale,
   return (uint32_t)cl;
 }
 
-// One warp per point, 32 coordinates per step. Lane j quantizes coordinate
-// 32m + j; a ballot per bit level gives the plane words directly, and lane l
-// stores plane l's word.
-__global__ void quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32,
-                                       const float* __restrict__ lo,
-                                       const float* __restrict__ scale, int bits,
-                                       uint32_t* __restrict__ planes) {
-  const int lane = threadIdx.x & 31;
+// One warp per point. The warp first copies the point's row into its
+// shared-memory slot (16-byte loads when rows are 16-byte aligned, all issued
+// before any is used), then quantizes 32 coordinates per step: lane j takes
+// coordinate 32m + j and eight ballots over the code (aligned to 8 bits) give
+// the plane words; lane l keeps plane l's word in shared memory. The point's
+// plane rows (W32 words each) are then written out contiguously.
+constexpr int QP_THREADS = 256;
+
+__global__ void __launch_bounds__(QP_THREADS)
+quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, const float* __restrict__ lo,
+                       const float* __restrict__ scale, int bits, int vec4, uint32_t* __restrict__ planes) {
+  extern __shared__ __align__(16) float qsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int dpad = (d + 3) & ~3;
+  const int wstride = (dpad + bits * W32 + 3) & ~3;  // floats per warp, keeps 16-byte alignment
+  float* row_s = qsm + (size_t)wib * wstride;
+  uint32_t* word_s = reinterpret_cast<uint32_t*>(row_s + dpad);  // [bits][W32]
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4;
   for (int64_t i = warp; i < n; i += nwarps) {
-    const float* row = x + i * d;
+    const float* row = x + (size_t)i * d;
+    if (vec4) {
+      for (int f = lane; f < (d >> 2); f += 32)
+        reinterpret_cast<float4*>(row_s)[f] = __ldg(reinterpret_cast<const float4*>(row) + f);
+    } else {
+      for (int c = lane; c < d; c += 32) row_s[c] = __ldg(row + c);
+    }
+    __syncwarp();
     for (int m = 0; m < W32; ++m) {
       const int c = m * 32 + lane;
       uint32_t code = 0;
-      if (c < d) code = quantize_one(__ldg(row + c), __ldg(lo + c), __ldg(scale + c), bits);
-      uint32_t mine = 0;
-      for (int l = 0; l < bits; ++l) {
-        const uint32_t word = __ballot_sync(0xffffffffu, (code >> (bits - 1 - l)) & 1u);
-        if (lane == l) mine = word;
-      }
-      if (lane < bits) planes[((size_t)lane * n + i) * W32 + m] = mine;
+      if (c < d) code = quantize_one(row_s[c], __ldg(lo + c), __ldg(scale + c), bits);
+      // plane l is bit 7 - l of the 8-bit-aligned code (words past `bits`
+      // are unused); lane l picks word l through a select tree on its lane bits
+      const uint32_t c8 = code << (8 - bits);
+      uint32_t w[8];
+#pragma unroll
+      for (int l = 0; l < 8; ++l) w[l] = __ballot_sync(0xffffffffu, c8 & (0x80u >> l));
+      const uint32_t s01 = b0 ? w[1] : w[0], s23 = b0 ? w[3] : w[2];
+      const uint32_t s45 = b0 ? w[5] : w[4], s67 = b0 ? w[7] : w[6];
+      const uint32_t s03 = b1 ? s23 : s01, s47 = b1 ? s67 : s45;
+      const uint32_t mine = b2 ? s47 : s03;
+      if (lane < bits) word_s[lane * W32 + m] = mine;
     }
+    __syncwarp();
+    for (int l = 0; l < bits; ++l)
+      for (int m = lane; m < W32; m += 32) planes[((size_t)l * n + i) * W32 + m] = word_s[l * W32 + m];
+    __syncwarp();
   }
 }
 
@@ -178,15 +222,21 @@ void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int
   else
     range_partial_kernel<1><<<blocks, RANGE_THREADS, 0, s>>>(x, total_vec, d, nthreads, pmin, pmax, err);
   hf_after_launch("range_partial_kernel", s);
-  range_final_kernel<<<hf_blocks(d, 128), 128, 0, s>>>(pmin, pmax, nthreads, vec, d, bits, lo, scale); hf_after_launch("range_final_kernel", s);
+  range_final_kernel<<<d, 256, 0, s>>>(pmin, pmax, nthreads, vec, d, bits, lo, scale);
+  hf_after_launch("range_final_kernel", s);
 }
 
 void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
                             int bits, uint32_t* planes, int* err, cudaStream_t s) {
   (void)err;
   const int W32 = (d + 31) / 32;
-  quantize_planes_kernel<<<hf_blocks(n * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, W32, lo, scale,
-                                                                             bits, planes); hf_after_launch("quantize_planes_kernel", s);
+  const int vec4 = d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  const size_t smem = (size_t)(QP_THREADS / 32) * ((((d + 3) & ~3) + bits * W32 + 3) & ~3) * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute((const void*)quantize_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  quantize_planes_kernel<<<hf_blocks(n * 32, QP_THREADS, 152 * 16), QP_THREADS, smem, s>>>(x, n, d, W32, lo, scale,
+                                                                                          bits, vec4, planes);
+  hf_after_launch("quantize_planes_kernel", s);
 }
 
 void launch_quantize_codes(const float* x, int64_t n, int d, const float* lo, const float* scale,
