@@ -105,6 +105,9 @@ int hf_build(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits,
  * key=value pairs (NULL or "" = defaults):
  *   prefix_words=K   64-bit key words sorted by radix (1..W, default min(2, W));
  *                    runs of equal prefixes are then ordered by the full key;
+ *   sort_batch=B     at most B trees keyed and sorted together (default: as
+ *                    many as fit in half of the free device memory, 16 GiB
+ *                    at most); the result does not depend on B;
  *   spin_limit_us=U  bound of each inter-block wait in the sort (default 2e6);
  *   test_stall=1     test hook: one block of the first sort pass waits on a
  *                    status word that nothing writes, so the bounded wait runs

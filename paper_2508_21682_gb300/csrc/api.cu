@@ -12,7 +12,7 @@
 
 #include "hf_internal.cuh"
 
-size_t sort_status_words(int64_t n, int K);
+size_t sort_status_words(int64_t n, int K, int tb);
 int tie_small_cap(int W, int d, int bits, int K, int K2);
 size_t tie_scratch_words(int W, int d, int bits, int K, int K2);
 
@@ -121,6 +121,9 @@ int parse_options(hf_forest* f, const char* opts) {
     if (key == "prefix_words") {
       if (v < 1 || v > 8) return HF_EINVAL;
       f->K = (int)v;
+    } else if (key == "sort_batch") {
+      if (v < 1) return HF_EINVAL;
+      f->sort_batch_max = (int)v;
     } else if (key == "spin_limit_us") {
       if (v < 1) return HF_EINVAL;
       f->spin_limit_us = v;
@@ -279,6 +282,20 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     f->x = f->x_owned;
   }
   const int K = f->K, W32 = f->W32;
+  // Trees are keyed and sorted in batches of TB (all of them when the
+  // batch's scratch fits in half of the free device memory, 16 GiB at most).
+  {
+    const int64_t ntiles = (n + 4095) / 4096;
+    const double per_tree = (double)n * (8.0 * f->K2 + 24.0) + (double)(ntiles + 1) * 256 * 4 * 8 * K;
+    size_t fr = 0, tot = 0;
+    double budget = 16.0 * (1ull << 30);
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && 0.5 * (double)fr < budget) budget = 0.5 * (double)fr;
+    else cudaGetLastError();
+    const double tbd = budget / per_tree;
+    f->TB = tbd >= T ? T : (tbd < 1.0 ? 1 : (int)tbd);
+    if (f->sort_batch_max > 0 && f->TB > f->sort_batch_max) f->TB = f->sort_batch_max;
+  }
+  const int TB = f->TB;
   chk(dalloc(&f->lo, d));
   chk(dalloc(&f->scale, d));
   chk(dalloc(&f->planes, (size_t)bits * n * W32));
@@ -287,13 +304,13 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   chk(dalloc(&f->prefix, (size_t)T * K * n));
   chk(dalloc(&f->sigma, (size_t)T * n));
   chk(dalloc(&f->err, 1));
-  chk(dalloc(&f->pk, (size_t)f->K2 * n));
-  chk(dalloc(&f->sort.keys_a, n));
-  chk(dalloc(&f->sort.keys_b, n));
-  chk(dalloc(&f->sort.vals_a, n));
-  chk(dalloc(&f->sort.vals_b, n));
-  chk(dalloc(&f->sort.status, sort_status_words(n, K)));
-  chk(dalloc(&f->sort.hist, (size_t)K * 8 * 256));
+  chk(dalloc(&f->pk, (size_t)TB * f->K2 * n));
+  chk(dalloc(&f->sort.keys_a, (size_t)TB * n));
+  chk(dalloc(&f->sort.keys_b, (size_t)TB * n));
+  chk(dalloc(&f->sort.vals_a, (size_t)TB * n));
+  chk(dalloc(&f->sort.vals_b, (size_t)TB * n));
+  chk(dalloc(&f->sort.status, sort_status_words(n, K, TB)));
+  chk(dalloc(&f->sort.hist, (size_t)TB * K * 8 * 256));
   const int cap = tie_small_cap(f->W, d, bits, K, f->K2);
   f->tie.big_cap = n / (cap + 1) + 1;
   chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1)));
@@ -328,11 +345,16 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   launch_quantize_planes(f->x, n, d, f->lo, f->scale, bits, f->planes, f->err, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(0, a0, a1);
-  for (int t = 0; t < T && rc == HF_OK; ++t) {
+  for (int t0 = 0; t0 < T && rc == HF_OK; t0 += TB) {
+    const int tb = T - t0 < TB ? T - t0 : TB;
     cudaEvent_t k0 = tm.mark();
-    launch_prefix_keys(f->planes, n, d, bits, f->K2, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32, f->pk, s);
+    for (int j = 0; j < tb; ++j) {
+      const int t = t0 + j;
+      launch_prefix_keys(f->planes, n, d, bits, f->K2, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32,
+                         f->pk + (size_t)j * f->K2 * n, s);
+    }
     cudaEvent_t k1 = tm.mark();
-    rc = sort_tree(f, t, s);
+    rc = sort_batch(f, t0, tb, s);
     cudaEvent_t k2 = tm.mark();
     tm.span(1, k0, k1);
     tm.span(2, k1, k2);
@@ -351,7 +373,10 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   cudaFree(rscratch);
   if (rc == HF_OK) {
     tm.collect({0, 1, 2, 3});
-    f->timings[6] = (float)(T * (1 + 2 + 8 * K + (K > 1 ? 1 : 0) + 3));
+    // keys, prefix gather and tie kernels per tree; histogram, scan and 8K
+    // passes per batch
+    const int nb = (T + TB - 1) / TB;
+    f->timings[6] = (float)(T * (1 + (K > 1 ? 1 : 0) + (K < f->W ? 2 : 0)) + nb * (2 + 8 * K));
   }
   free_build_scratch(f);
   if (rc != HF_OK) {

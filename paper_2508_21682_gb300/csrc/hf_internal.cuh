@@ -22,13 +22,13 @@ __device__ __forceinline__ void hf_raise(int* err, int bit) { atomicOr(err, bit)
 // ---------------------------------------------------------------------------
 // The forest handle.
 // ---------------------------------------------------------------------------
-struct SortScratch {
-  uint64_t* keys_a = nullptr;  // [n]
-  uint64_t* keys_b = nullptr;  // [n]
-  uint32_t* vals_a = nullptr;  // [n]
-  uint32_t* vals_b = nullptr;  // [n]
-  uint32_t* status = nullptr;  // [passes][tiles + 1][256] look-back words + tickets
-  uint32_t* hist = nullptr;    // [K*8][256] digit counts -> exclusive offsets
+struct SortScratch {  // for a batch of TB trees
+  uint64_t* keys_a = nullptr;  // [TB][n]
+  uint64_t* keys_b = nullptr;  // [TB][n]
+  uint32_t* vals_a = nullptr;  // [TB][n]
+  uint32_t* vals_b = nullptr;  // [TB][n]
+  uint32_t* status = nullptr;  // [passes]([TB][tiles + 1][256] look-back words, ticket)
+  uint32_t* hist = nullptr;    // [TB][K*8][256] digit counts -> exclusive offsets
 };
 
 struct TieScratch {
@@ -65,13 +65,15 @@ struct hf_forest {
   void* xb = nullptr;
   float* xnrm = nullptr;
 
-  uint64_t* pk = nullptr;     // [K2][n] key words in point order (scratch)
+  uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
+  int TB = 1;                 // trees keyed and sorted together
   SortScratch sort;
   TieScratch tie;
 
   // options
   int64_t spin_limit_us = 2000000;
   int test_stall = 0;
+  int sort_batch_max = 0;  // cap on trees per sort batch (0: by memory)
   int mode = 0;
   int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
   int timing = 1;
@@ -104,7 +106,7 @@ void launch_full_keys_codes(const uint8_t* codes, int64_t n, int d, int bits, in
                             cudaStream_t s);
 
 // sort.cu
-int sort_tree(hf_forest* f, int tree, cudaStream_t s);  // keys -> sigma, prefix
+int sort_batch(hf_forest* f, int t0, int tb, cudaStream_t s);  // keys of trees t0.. -> sigma, prefix
 int tie_fixup_big(hf_forest* f, int tree, uint32_t big_runs, cudaStream_t s);
 
 // window.cu

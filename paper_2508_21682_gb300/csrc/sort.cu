@@ -10,6 +10,11 @@
 // equal prefixes stay in index order; the fix-up then reorders each run of
 // equal prefixes by its full keys.
 //
+// The trees of a batch are sorted together: one launch per pass covers every
+// tree, and tile tickets interleave the trees (ticket g is tile g / TB of tree
+// g % TB), so the tiles in flight at any time are spread over all trees and
+// each tree's look-back chain stays short.
+//
 // The look-back is the only wait between blocks. Tiles take tickets from an
 // atomic counter, so a tile only ever waits for tiles that started before it;
 // each wait is bounded by a %globaltimer deadline, after which the tile sets
@@ -53,9 +58,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Digit histograms of all 8 bytes of all K prefix words (order-independent).
-__global__ void digit_hist_kernel(const uint64_t* __restrict__ pk, int64_t n, int K,
+// Tree blockIdx.y: keys at pk + y * pk_ts, histograms at hist + y * K * 8 * 256.
+__global__ void digit_hist_kernel(const uint64_t* __restrict__ pk, int64_t pk_ts, int64_t n, int K,
                                   uint32_t* __restrict__ hist) {
   extern __shared__ uint32_t sh[];  // [K*8][256]
+  pk += blockIdx.y * pk_ts;
+  hist += (size_t)blockIdx.y * K * 8 * 256;
   const int nh = K * 8 * 256;
   for (int i = threadIdx.x; i < nh; i += blockDim.x) sh[i] = 0;
   __syncthreads();
@@ -100,25 +108,53 @@ struct PassSmem {
   uint32_t tile;
 };
 
+// One pass over the trees of a batch. Each array is given as the first
+// tree's pointer plus the element stride between trees.
+struct PassArgs {
+  const uint64_t* keys_in;
+  int64_t keys_in_ts;
+  const uint32_t* vals_in;  // null: identity (first pass)
+  int64_t vals_in_ts;
+  const uint64_t* gather_src;
+  int64_t gather_src_ts;
+  uint64_t* keys_out;
+  int64_t keys_out_ts;
+  uint32_t* vals_out;
+  int64_t vals_out_ts;
+  const uint32_t* goff;  // exclusive digit offsets of this pass
+  int64_t goff_ts;
+  uint32_t* status;      // [TB][ntiles + 1][256]
+  uint32_t* ticket;
+  int* err;
+  int64_t n, ntiles;
+  uint64_t spin_ns;
+  int shift, TB, stall;
+};
+
 // One LSD pass: bins the keys of one tile by `digit = key >> shift & 255`.
 // GATHER: the key of the element at position e is gather_src[vals_in[e]]
 // (the next prefix word, fetched in the current order).
 template <bool GATHER>
-__global__ void __launch_bounds__(NT)
-onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                const uint64_t* __restrict__ gather_src, uint64_t* __restrict__ keys_out,
-                uint32_t* __restrict__ vals_out, int64_t n, int shift,
-                const uint32_t* __restrict__ goff, uint32_t* __restrict__ status,
-                uint32_t* __restrict__ ticket, int* __restrict__ err, uint64_t spin_ns,
-                int stall, int64_t ntiles) {
+__global__ void __launch_bounds__(NT) onesweep_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   PassSmem& S = *reinterpret_cast<PassSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  if (tid == 0) S.tile = atomicAdd(ticket, 1u);
+  if (tid == 0) S.tile = atomicAdd(a.ticket, 1u);
   for (int i = tid; i < WARPS * 256; i += NT) (&S.whist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t tile = S.tile;
+  const int64_t tr = S.tile % (uint32_t)a.TB;
+  const int64_t tile = S.tile / (uint32_t)a.TB;
+  const int64_t n = a.n, ntiles = a.ntiles;
+  const int shift = a.shift;
+  const uint64_t* __restrict__ keys_in = GATHER ? nullptr : a.keys_in + tr * a.keys_in_ts;
+  const uint32_t* __restrict__ vals_in = a.vals_in ? a.vals_in + tr * a.vals_in_ts : nullptr;
+  const uint64_t* __restrict__ gather_src = GATHER ? a.gather_src + tr * a.gather_src_ts : nullptr;
+  uint64_t* __restrict__ keys_out = a.keys_out + tr * a.keys_out_ts;
+  uint32_t* __restrict__ vals_out = a.vals_out + tr * a.vals_out_ts;
+  const uint32_t* __restrict__ goff = a.goff + tr * a.goff_ts;
+  uint32_t* __restrict__ status = a.status + (size_t)tr * (ntiles + 1) * 256;
+  int* err = a.err;
   const int64_t base = tile * TILE;
 
   uint64_t k[IPT];
@@ -192,7 +228,7 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
       for (int i = 0; i < LB; ++i) {
         // test hook: tile 1 watches the spare status row that nothing writes
         const int64_t pt = pred - i;
-        const uint32_t* ps = (stall && tile == 1) ? status + ntiles * 256 + dgt : status + pt * 256 + dgt;
+        const uint32_t* ps = (a.stall && tr == 0 && tile == 1) ? status + ntiles * 256 + dgt : status + pt * 256 + dgt;
         sv[i] = pt >= 0 ? ld_relaxed(ps) : FLAG_PRE;  // before tile 0: prefix 0
       }
       int used = 0;
@@ -211,7 +247,7 @@ onesweep_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict
       }
       if (done) break;
       pred -= used;
-      if (used == 0 && (++spins & 15u) == 0 && (globaltimer() - t0 > spin_ns || spins > (1u << 28))) {
+      if (used == 0 && (++spins & 15u) == 0 && (globaltimer() - t0 > a.spin_ns || spins > (1u << 28))) {
         hf_raise(err, HF_ERRBIT_TIMEOUT);
         break;
       }
@@ -487,75 +523,107 @@ static cudaError_t set_attr(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-int sort_tree(hf_forest* f, int t, cudaStream_t s) {
+// Sorts trees t0 .. t0 + tb - 1 (their key words are at f->pk, tree j of the
+// batch at f->pk + j * K2 * n) into f->prefix / f->sigma, then fixes each
+// tree's runs of equal prefixes.
+int sort_batch(hf_forest* f, int t0, int tb, cudaStream_t s) {
   const int64_t n = f->n;
-  const int K = f->K;
+  const int K = f->K, K2 = f->K2;
   const int64_t ntiles = (n + TILE - 1) / TILE;
   const int passes = 8 * K;
-  const size_t per_pass = (size_t)(ntiles + 1) * 256 + 1;  // status rows + spare row + ticket
+  const size_t per_pass = (size_t)tb * (ntiles + 1) * 256 + 1;  // status rows (+ spare row per tree) + ticket
+  const int64_t pk_ts = (int64_t)K2 * n;
+  const int64_t hist_ts = (int64_t)K * 8 * 256;
   uint32_t* status = f->sort.status;
-  uint64_t* pre = f->prefix + (size_t)t * K * n;
-  uint32_t* sig = f->sigma + (size_t)t * n;
 
-  cudaMemsetAsync(f->sort.hist, 0, (size_t)K * 8 * 256 * sizeof(uint32_t), s);
+  cudaMemsetAsync(f->sort.hist, 0, (size_t)tb * hist_ts * sizeof(uint32_t), s);
   cudaMemsetAsync(status, 0, per_pass * passes * sizeof(uint32_t), s);
-  const size_t hsm = (size_t)K * 8 * 256 * sizeof(uint32_t);
+  const size_t hsm = (size_t)hist_ts * sizeof(uint32_t);
   set_attr((const void*)digit_hist_kernel, hsm);
-  digit_hist_kernel<<<hf_blocks(n, 512, 152 * 2), 512, hsm, s>>>(f->pk, n, K, f->sort.hist); hf_after_launch("digit_hist_kernel", s);
-  hist_scan_kernel<<<K * 8, 256, 0, s>>>(f->sort.hist); hf_after_launch("hist_scan_kernel", s);
+  digit_hist_kernel<<<dim3(hf_blocks(n, 512, 152 * 2 / tb + 1), (unsigned)tb), 512, hsm, s>>>(f->pk, pk_ts, n, K,
+                                                                                            f->sort.hist);
+  hf_after_launch("digit_hist_kernel", s);
+  hist_scan_kernel<<<(unsigned)(tb * K * 8), 256, 0, s>>>(f->sort.hist);
+  hf_after_launch("hist_scan_kernel", s);
 
   const size_t psm = sizeof(PassSmem);
   set_attr((const void*)onesweep_kernel<false>, psm);
   set_attr((const void*)onesweep_kernel<true>, psm);
 
-  const uint64_t spin_ns = (uint64_t)f->spin_limit_us * 1000ull;
-  const uint64_t* kin = nullptr;
-  const uint32_t* vin = nullptr;  // identity
+  PassArgs a{};
+  a.err = f->err;
+  a.n = n;
+  a.ntiles = ntiles;
+  a.spin_ns = (uint64_t)f->spin_limit_us * 1000ull;
+  a.TB = tb;
+  a.goff_ts = hist_ts;
+  a.gather_src_ts = pk_ts;
+  const unsigned grid = (unsigned)(ntiles * tb);
   int pass = 0;
   for (int w = K - 1; w >= 0; --w) {
     for (int b = 0; b < 8; ++b, ++pass) {
       const bool gather = (w < K - 1) && b == 0;
       const bool last = pass == passes - 1;
-      uint64_t* kout = last ? pre : ((pass & 1) ? f->sort.keys_b : f->sort.keys_a);
-      uint32_t* vout = last ? sig : ((pass & 1) ? f->sort.vals_b : f->sort.vals_a);
-      const uint64_t* src = (w == K - 1 && b == 0) ? f->pk + (size_t)(K - 1) * n : kin;
-      uint32_t* st = status + per_pass * pass;
-      uint32_t* ticket = st + (size_t)(ntiles + 1) * 256;
-      const uint32_t* goff = f->sort.hist + (size_t)(w * 8 + b) * 256;
-      const int stall = (f->test_stall && pass == 0) ? 1 : 0;
+      if (pass == 0) {
+        a.keys_in = f->pk + (size_t)(K - 1) * n;
+        a.keys_in_ts = pk_ts;
+        a.vals_in = nullptr;
+        a.vals_in_ts = 0;
+      }
+      a.gather_src = gather ? f->pk + (size_t)w * n : nullptr;
+      if (last) {
+        a.keys_out = f->prefix + (size_t)t0 * K * n;  // word 0 of each tree's prefix
+        a.keys_out_ts = (int64_t)K * n;
+        a.vals_out = f->sigma + (size_t)t0 * n;
+        a.vals_out_ts = n;
+      } else {
+        a.keys_out = (pass & 1) ? f->sort.keys_b : f->sort.keys_a;
+        a.keys_out_ts = n;
+        a.vals_out = (pass & 1) ? f->sort.vals_b : f->sort.vals_a;
+        a.vals_out_ts = n;
+      }
+      a.goff = f->sort.hist + (size_t)(w * 8 + b) * 256;
+      a.status = status + per_pass * pass;
+      a.ticket = a.status + (size_t)tb * (ntiles + 1) * 256;
+      a.shift = 8 * b;
+      a.stall = (f->test_stall && pass == 0) ? 1 : 0;
       if (gather)
-        onesweep_kernel<true><<<(unsigned)ntiles, NT, psm, s>>>(nullptr, vin, f->pk + (size_t)w * n, kout, vout,
-                                                                n, 8 * b, goff, st, ticket, f->err, spin_ns,
-                                                                stall, ntiles);
+        onesweep_kernel<true><<<grid, NT, psm, s>>>(a);
       else
-        onesweep_kernel<false><<<(unsigned)ntiles, NT, psm, s>>>(src, vin, nullptr, kout, vout, n, 8 * b, goff,
-                                                                 st, ticket, f->err, spin_ns, stall, ntiles);
+        onesweep_kernel<false><<<grid, NT, psm, s>>>(a);
       hf_after_launch("onesweep_kernel", s);
-      kin = kout;
-      vin = vout;
+      a.keys_in = a.keys_out;
+      a.keys_in_ts = a.keys_out_ts;
+      a.vals_in = a.vals_out;
+      a.vals_in_ts = a.vals_out_ts;
     }
   }
-  if (K > 1) {
-    gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(f->pk, sig, n, K, pre, f->err);
-    hf_after_launch("gather_prefix_kernel", s);
-  }
-
-  // Equal prefixes: find runs, fix the small ones on the device right away.
-  // With K == W the prefix is the whole key: equal prefixes are equal keys,
-  // already in index order.
-  if (K < f->W) {
-    const TieGeom tg = tie_geom(f->W, f->d, f->bits, K, f->K2);
-    uint32_t* ctr = f->tie.counters + (size_t)t * 4;
-    cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
-    tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, tg.cap, f->tie.runs,
-                                                              f->tie.big_runs + (size_t)t * f->tie.big_cap,
-                                                              f->tie.big_cap, ctr);
-    hf_after_launch("tie_find_kernel", s);
-    set_attr((const void*)tie_small_kernel, tg.smem);
-    tie_small_kernel<<<TIE_BLOCKS, TIE_THREADS, tg.smem, s>>>(
-        f->planes, n, f->d, f->W32, f->bits, f->W, K, tg.K2, tg.Lf, tg.cap, f->pk, f->K2, f->pi + (size_t)t * f->d,
-        f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->tie.fk, f->err);
-    hf_after_launch("tie_small_kernel", s);
+  for (int j = 0; j < tb; ++j) {
+    const int t = t0 + j;
+    const uint64_t* pkt = f->pk + (size_t)j * pk_ts;
+    uint64_t* pre = f->prefix + (size_t)t * K * n;
+    uint32_t* sig = f->sigma + (size_t)t * n;
+    if (K > 1) {
+      gather_prefix_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pkt, sig, n, K, pre, f->err);
+      hf_after_launch("gather_prefix_kernel", s);
+    }
+    // Equal prefixes: find runs, fix the small ones on the device right
+    // away. With K == W the prefix is the whole key: equal prefixes are equal
+    // keys, already in index order.
+    if (K < f->W) {
+      const TieGeom tg = tie_geom(f->W, f->d, f->bits, K, K2);
+      uint32_t* ctr = f->tie.counters + (size_t)t * 4;
+      cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s);
+      tie_find_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(pre, n, K, tg.cap, f->tie.runs,
+                                                                f->tie.big_runs + (size_t)t * f->tie.big_cap,
+                                                                f->tie.big_cap, ctr);
+      hf_after_launch("tie_find_kernel", s);
+      set_attr((const void*)tie_small_kernel, tg.smem);
+      tie_small_kernel<<<TIE_BLOCKS, TIE_THREADS, tg.smem, s>>>(
+          f->planes, n, f->d, f->W32, f->bits, f->W, K, tg.K2, tg.Lf, tg.cap, pkt, K2, f->pi + (size_t)t * f->d,
+          f->rbits + (size_t)t * f->W32, f->tie.runs, ctr, sig, f->tie.fk, f->err);
+      hf_after_launch("tie_small_kernel", s);
+    }
   }
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
@@ -619,9 +687,9 @@ size_t tie_scratch_words(int W, int d, int bits, int K, int K2) {
   return (size_t)TIE_BLOCKS * g.cap * W;
 }
 
-size_t sort_status_words(int64_t n, int K) {
+size_t sort_status_words(int64_t n, int K, int tb) {
   const int64_t ntiles = (n + TILE - 1) / TILE;
-  return ((size_t)(ntiles + 1) * 256 + 1) * 8 * K;
+  return ((size_t)tb * (ntiles + 1) * 256 + 1) * 8 * K;
 }
 
 int tie_small_cap(int W, int d, int bits, int K, int K2) { return tie_geom(W, d, bits, K, K2).cap; }

@@ -72,6 +72,9 @@ def build_both(hf, x, T, bits, seed=S.SEED_FOREST, options=None):
     (3001, 33, 2, 5, None),              # d*b not a multiple of 64
     (2500, 384, 2, 8, "prefix_words=1"), # many equal prefixes -> tie fix-up
     (3000, 7, 2, 2, None),               # coarse codes: many equal full keys
+    (6007, 384, 5, 8, "sort_batch=2"),   # trees sorted in batches of 2, 2, 1
+    (4001, 64, 4, 8, "sort_batch=3,prefix_words=1"),  # batches of 3, 1 with many ties
+    (2999, 40, 3, 8, "sort_batch=1"),    # one tree per batch
 ])
 def test_codes_keys_order_bit_exact(hf, n, d, T, bits, opts):
     x = S.gaussian_mixture(n, d, n_components=50, seed=S.SEED_DATA)
@@ -88,8 +91,8 @@ def test_duplicate_points_order(hf):
     x = S.unit_gaussian(6000, 384, seed=5)
     x[1000:3500] = x[7]  # 2501 copies of one point -> one run longer than the on-device cap
     x[4000:4100] = x[11]
-    G, F = build_both(hf, x, 2, 8, options="prefix_words=1")
-    for t in range(2):
+    G, F = build_both(hf, x, 3, 8, options="prefix_words=1,sort_batch=2")
+    for t in range(3):
         assert np.array_equal(G.order(t).astype(np.int64), F.sigma[t])
     G.close()
 
