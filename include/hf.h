@@ -174,6 +174,18 @@ int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, 
 /* hf_free -- releases the forest and everything it owns (NULL is a no-op). */
 int hf_free(hf_forest* f);
 
+/*
+ * hf_trim_pool -- device memory of the library (forests and per-call
+ * scratch) comes from a library-owned, stream-ordered pool on each device, so
+ * that memory freed by one call is reused by the next without a device-wide
+ * synchronisation. Up to a quarter of the device's memory (64 GiB at most)
+ * stays cached in the pool after it is freed. hf_trim_pool waits for the
+ * current device and returns that device's cached memory to the driver, for
+ * callers that share the GPU with other allocators. Not part of the paper's
+ * method. Returns HF_OK or HF_ECUDA.
+ */
+int hf_trim_pool(void);
+
 /* hf_status_string -- static text for a status code (never NULL). */
 const char* hf_status_string(int status);
 

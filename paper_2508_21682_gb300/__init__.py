@@ -30,7 +30,7 @@ SYMBOLS = [
     "hf_build", "hf_build_opts", "hf_knn_graph", "hf_search", "hf_free", "hf_status_string",
     "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
     "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
-    "hf_launch_count", "hf_search_static",
+    "hf_launch_count", "hf_search_static", "hf_trim_pool",
 ]
 
 _lib = None
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
         "hf_debug_keys_from_codes": [vp, i64, i32, i32, vp, vp],
         "hf_launch_count": [],
         "hf_search_static": [vp, vp, i64, i32, i32, vp, vp, vp],
+        "hf_trim_pool": [],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -114,6 +115,11 @@ def _stream(*arrays):
 def launch_count() -> int:
     """Kernels launched by libhf.so in this process so far."""
     return int(lib().hf_launch_count())
+
+
+def trim_pool():
+    """Returns the current device's cached library memory to the driver."""
+    _check(lib().hf_trim_pool(), "hf_trim_pool")
 
 
 def tree_params(seed: int, tree: int, d: int):

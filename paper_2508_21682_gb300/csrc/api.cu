@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -38,16 +39,55 @@ int classify(const void* p) {
   return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
-template <typename T>
-cudaError_t dalloc(T** p, size_t count) {
+// Device memory comes from a library-owned, stream-ordered pool per device:
+// a buffer freed at the end of one call (on that call's stream) is handed to
+// the next call without a device-wide synchronisation or a trip to the
+// driver. The pool keeps up to a quarter of the device's memory (64 GiB at
+// most) cached between calls; hf_trim_pool returns it.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    size_t fr = 0, tot = 0;
+    uint64_t keep = 64ull << 30;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && tot / 4 < keep) keep = tot / 4;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+cudaError_t dalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
 }
 
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(reinterpret_cast<void*>(p));
+cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
+  void* v = nullptr;
+  const cudaError_t e = dalloc_bytes(&v, (count ? count : 1) * sizeof(T), s);
+  *p = static_cast<T*>(v);
+  return e;
+}
+
+// Frees in stream order on s: the caller has finished (or enqueued on s)
+// every use of p.
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(reinterpret_cast<void*>(p), s);
   p = nullptr;
 }
 
@@ -71,34 +111,34 @@ int finish(hf_forest* f, cudaStream_t s) {
   return HF_OK;
 }
 
-void free_build_scratch(hf_forest* f) {
-  dfree(f->pk);
-  dfree(f->sort.keys_a);
-  dfree(f->sort.keys_b);
-  dfree(f->sort.vals_a);
-  dfree(f->sort.vals_b);
-  dfree(f->sort.status);
-  dfree(f->sort.hist);
-  dfree(f->tie.runs);
-  dfree(f->tie.big_runs);
-  dfree(f->tie.counters);
-  dfree(f->tie.fk);
+void free_build_scratch(hf_forest* f, cudaStream_t s) {
+  dfree(f->pk, s);
+  dfree(f->sort.keys_a, s);
+  dfree(f->sort.keys_b, s);
+  dfree(f->sort.vals_a, s);
+  dfree(f->sort.vals_b, s);
+  dfree(f->sort.status, s);
+  dfree(f->sort.hist, s);
+  dfree(f->tie.runs, s);
+  dfree(f->tie.big_runs, s);
+  dfree(f->tie.counters, s);
+  dfree(f->tie.fk, s);
 }
 
-void destroy(hf_forest* f) {
+void destroy(hf_forest* f, cudaStream_t s) {
   if (!f) return;
-  free_build_scratch(f);
-  dfree(f->x_owned);
-  dfree(f->lo);
-  dfree(f->scale);
-  dfree(f->planes);
-  dfree(f->pi);
-  dfree(f->rbits);
-  dfree(f->prefix);
-  dfree(f->sigma);
-  dfree(f->err);
-  if (f->xb) cudaFree(f->xb);
-  dfree(f->xnrm);
+  free_build_scratch(f, s);
+  dfree(f->x_owned, s);
+  dfree(f->lo, s);
+  dfree(f->scale, s);
+  dfree(f->planes, s);
+  dfree(f->pi, s);
+  dfree(f->rbits, s);
+  dfree(f->prefix, s);
+  dfree(f->sigma, s);
+  dfree(f->err, s);
+  dfree(f->xb, s);
+  dfree(f->xnrm, s);
   delete f;
 }
 
@@ -276,7 +316,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   if (dev == 1) {
     f->x = points;
   } else {
-    chk(dalloc(&f->x_owned, (size_t)n * d));
+    chk(dalloc(&f->x_owned, (size_t)n * d, s));
     if (e == cudaSuccess)
       chk(cudaMemcpyAsync(f->x_owned, points, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, s));
     f->x = f->x_owned;
@@ -296,33 +336,33 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     if (f->sort_batch_max > 0 && f->TB > f->sort_batch_max) f->TB = f->sort_batch_max;
   }
   const int TB = f->TB;
-  chk(dalloc(&f->lo, d));
-  chk(dalloc(&f->scale, d));
-  chk(dalloc(&f->planes, (size_t)bits * n * W32));
-  chk(dalloc(&f->pi, (size_t)T * d));
-  chk(dalloc(&f->rbits, (size_t)T * W32));
-  chk(dalloc(&f->prefix, (size_t)T * K * n));
-  chk(dalloc(&f->sigma, (size_t)T * n));
-  chk(dalloc(&f->err, 1));
-  chk(dalloc(&f->pk, (size_t)TB * f->K2 * n));
-  chk(dalloc(&f->sort.keys_a, (size_t)TB * n));
-  chk(dalloc(&f->sort.keys_b, (size_t)TB * n));
-  chk(dalloc(&f->sort.vals_a, (size_t)TB * n));
-  chk(dalloc(&f->sort.vals_b, (size_t)TB * n));
-  chk(dalloc(&f->sort.status, sort_status_words(n, K, TB)));
-  chk(dalloc(&f->sort.hist, (size_t)TB * K * 8 * 256));
+  chk(dalloc(&f->lo, d, s));
+  chk(dalloc(&f->scale, d, s));
+  chk(dalloc(&f->planes, (size_t)bits * n * W32, s));
+  chk(dalloc(&f->pi, (size_t)T * d, s));
+  chk(dalloc(&f->rbits, (size_t)T * W32, s));
+  chk(dalloc(&f->prefix, (size_t)T * K * n, s));
+  chk(dalloc(&f->sigma, (size_t)T * n, s));
+  chk(dalloc(&f->err, 1, s));
+  chk(dalloc(&f->pk, (size_t)TB * f->K2 * n, s));
+  chk(dalloc(&f->sort.keys_a, (size_t)TB * n, s));
+  chk(dalloc(&f->sort.keys_b, (size_t)TB * n, s));
+  chk(dalloc(&f->sort.vals_a, (size_t)TB * n, s));
+  chk(dalloc(&f->sort.vals_b, (size_t)TB * n, s));
+  chk(dalloc(&f->sort.status, sort_status_words(n, K, TB), s));
+  chk(dalloc(&f->sort.hist, (size_t)TB * K * 8 * 256, s));
   const int cap = tie_small_cap(f->W, d, bits, K, f->K2);
   f->tie.big_cap = n / (cap + 1) + 1;
-  chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1)));
-  chk(dalloc(&f->tie.big_runs, (size_t)T * f->tie.big_cap));
-  chk(dalloc(&f->tie.counters, (size_t)T * 4));
-  chk(dalloc(&f->tie.fk, K < f->W ? tie_scratch_words(f->W, d, bits, K, f->K2) : 1));
+  chk(dalloc(&f->tie.runs, (size_t)(n / 2 + 1), s));
+  chk(dalloc(&f->tie.big_runs, (size_t)T * f->tie.big_cap, s));
+  chk(dalloc(&f->tie.counters, (size_t)T * 4, s));
+  chk(dalloc(&f->tie.fk, K < f->W ? tie_scratch_words(f->W, d, bits, K, f->K2) : 1, s));
   void* rscratch = nullptr;
   const size_t rbytes = range_scratch_bytes(n, d);
-  chk(cudaMalloc(&rscratch, rbytes));
+  chk(dalloc_bytes(&rscratch, rbytes, s));
   if (e != cudaSuccess) {
-    cudaFree(rscratch);
-    destroy(f);
+    dfree(rscratch, s);
+    destroy(f, s);
     return map_cuda(e);
   }
   cudaMemsetAsync(f->err, 0, sizeof(int), s);
@@ -370,7 +410,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     tm.span(3, b0, b1);
     if (rc == HF_OK) rc = finish(f, s);
   }
-  cudaFree(rscratch);
+  dfree(rscratch, s);
   if (rc == HF_OK) {
     tm.collect({0, 1, 2, 3});
     // keys, prefix gather and tie kernels per tree; histogram, scan and 8K
@@ -378,9 +418,9 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     const int nb = (T + TB - 1) / TB;
     f->timings[6] = (float)(T * (1 + (K > 1 ? 1 : 0) + (K < f->W ? 2 : 0)) + nb * (2 + 8 * K));
   }
-  free_build_scratch(f);
+  free_build_scratch(f, s);
   if (rc != HF_OK) {
-    destroy(f);
+    destroy(f, s);
     return rc;
   }
   *out = f;
@@ -389,8 +429,18 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
 
 int hf_free(hf_forest* f) {
   if (!f) return HF_OK;
-  cudaDeviceSynchronize();
-  destroy(f);
+  cudaDeviceSynchronize();  // no use of the forest's memory is still in flight
+  destroy(f, 0);
+  return HF_OK;
+}
+
+int hf_trim_pool(void) {
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return HF_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return HF_ECUDA;
+  }
   return HF_OK;
 }
 
@@ -439,16 +489,16 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   const int kp = window_list_pitch(tensor ? k + slack : k);
   uint32_t* li = nullptr;
   float* ldd = nullptr;
-  cudaError_t e = dalloc(&li, (size_t)n * kp);
-  if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp);
+  cudaError_t e = dalloc(&li, (size_t)n * kp, s);
+  if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp, s);
   if (e == cudaSuccess && tensor && !f->xb) {
-    e = cudaMalloc(&f->xb, (size_t)n * bf16_pitch(f->d) * 2);
-    if (e == cudaSuccess) e = dalloc(&f->xnrm, (size_t)n);
+    e = dalloc_bytes(&f->xb, (size_t)n * bf16_pitch(f->d) * 2, s);
+    if (e == cudaSuccess) e = dalloc(&f->xnrm, (size_t)n, s);
     if (e == cudaSuccess) launch_prepare_bf16(f->x, n, f->d, f->xb, f->xnrm, s);
   }
   if (e != cudaSuccess) {
-    dfree(li);
-    dfree(ldd);
+    dfree(li, s);
+    dfree(ldd, s);
     return map_cuda(e);
   }
   Timer tm(f, s);
@@ -474,8 +524,8 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
   if (rc == HF_OK) tm.collect({4});
-  dfree(li);
-  dfree(ldd);
+  dfree(li, s);
+  dfree(ldd, s);
   return rc;
 }
 
@@ -495,10 +545,10 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
   uint32_t* li = dev_i ? reinterpret_cast<uint32_t*>(out_idx) : nullptr;
   float* ldd = dev_d ? out_dist : nullptr;
   cudaError_t e = cudaSuccess;
-  if (!dev_q) e = dalloc(&qd, (size_t)nq * d);
-  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d);
-  if (e == cudaSuccess && !li) e = dalloc(&li, cnt);
-  if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt);
+  if (!dev_q) e = dalloc(&qd, (size_t)nq * d, s);
+  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d, s);
+  if (e == cudaSuccess && !li) e = dalloc(&li, cnt, s);
+  if (e == cudaSuccess && !ldd) e = dalloc(&ldd, cnt, s);
   int rc = map_cuda(e);
   Timer tm(f, s);
   if (rc == HF_OK) {
@@ -515,10 +565,10 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
     if (rc == HF_OK) rc = rc2;
     if (rc == HF_OK) tm.collect({5});
   }
-  dfree(qd);
-  dfree(qc);
-  if (!dev_i) dfree(li);
-  if (!dev_d) dfree(ldd);
+  dfree(qd, s);
+  dfree(qc, s);
+  if (!dev_i) dfree(li, s);
+  if (!dev_d) dfree(ldd, s);
   return rc;
 }
 
@@ -531,12 +581,12 @@ int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream) {
   const size_t cnt = (size_t)f->n * f->d;
   const bool dev = classify(out_codes) == 1;
   uint8_t* c = dev ? out_codes : nullptr;
-  if (!dev && dalloc(&c, cnt) != cudaSuccess) return HF_ENOMEM;
+  if (!dev && dalloc(&c, cnt, s) != cudaSuccess) return HF_ENOMEM;
   launch_planes_to_codes(f->planes, f->n, f->d, f->bits, c, s);
   int rc = HF_OK;
   if (!dev) rc = map_cuda(cudaMemcpyAsync(out_codes, c, cnt, cudaMemcpyDeviceToHost, s));
   int rc2 = finish(f, s);
-  if (!dev) dfree(c);
+  if (!dev) dfree(c, s);
   return rc ? rc : rc2;
 }
 
@@ -547,13 +597,13 @@ int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream) 
   const size_t cnt = (size_t)f->n * f->W;
   const bool dev = classify(out_keys) == 1;
   uint64_t* kk = dev ? out_keys : nullptr;
-  if (!dev && dalloc(&kk, cnt) != cudaSuccess) return HF_ENOMEM;
+  if (!dev && dalloc(&kk, cnt, s) != cudaSuccess) return HF_ENOMEM;
   launch_full_keys_planes(f->planes, f->n, f->d, f->bits, f->W, f->pi + (size_t)tree * f->d,
                           f->rbits + (size_t)tree * f->W32, kk, s);
   int rc = HF_OK;
   if (!dev) rc = map_cuda(cudaMemcpyAsync(out_keys, kk, cnt * 8, cudaMemcpyDeviceToHost, s));
   int rc2 = finish(f, s);
-  if (!dev) dfree(kk);
+  if (!dev) dfree(kk, s);
   return rc ? rc : rc2;
 }
 
@@ -580,9 +630,9 @@ int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq
   uint8_t* qc = nullptr;
   int64_t* po = dev_o ? out_pos : nullptr;
   cudaError_t e = cudaSuccess;
-  if (!dev_q) e = dalloc(&qd, (size_t)nq * d);
-  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d);
-  if (e == cudaSuccess && !po) e = dalloc(&po, (size_t)nq);
+  if (!dev_q) e = dalloc(&qd, (size_t)nq * d, s);
+  if (e == cudaSuccess) e = dalloc(&qc, (size_t)nq * d, s);
+  if (e == cudaSuccess && !po) e = dalloc(&po, (size_t)nq, s);
   int rc = map_cuda(e);
   if (rc == HF_OK) {
     if (!dev_q) cudaMemcpyAsync(qd, queries, (size_t)nq * d * 4, cudaMemcpyHostToDevice, s);
@@ -593,9 +643,9 @@ int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq
     int rc2 = finish(f, s);
     if (rc == HF_OK) rc = rc2;
   }
-  dfree(qd);
-  dfree(qc);
-  if (!dev_o) dfree(po);
+  dfree(qd, s);
+  dfree(qc, s);
+  if (!dev_o) dfree(po, s);
   return rc;
 }
 
@@ -610,8 +660,8 @@ int hf_debug_keys_from_codes(const uint8_t* codes, int64_t n, int32_t d, int32_t
   uint8_t* cd = nullptr;
   uint64_t* kk = dev_o ? out_keys : nullptr;
   cudaError_t e = cudaSuccess;
-  if (!dev_c) e = dalloc(&cd, (size_t)n * d);
-  if (e == cudaSuccess && !kk) e = dalloc(&kk, (size_t)n * W);
+  if (!dev_c) e = dalloc(&cd, (size_t)n * d, s);
+  if (e == cudaSuccess && !kk) e = dalloc(&kk, (size_t)n * W, s);
   int rc = map_cuda(e);
   if (rc == HF_OK) {
     if (!dev_c) cudaMemcpyAsync(cd, codes, (size_t)n * d, cudaMemcpyHostToDevice, s);
@@ -621,8 +671,8 @@ int hf_debug_keys_from_codes(const uint8_t* codes, int64_t n, int32_t d, int32_t
     if (se == cudaSuccess) se = cudaGetLastError();
     rc = map_cuda(se);
   }
-  dfree(cd);
-  if (!dev_o) dfree(kk);
+  dfree(cd, s);
+  if (!dev_o) dfree(kk, s);
   return rc;
 }
 

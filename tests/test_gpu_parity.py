@@ -249,3 +249,18 @@ def test_tensor_mode_graph(hf, n, d, T, w, k, mixture):
     hits = sum(len(set(a[a >= 0].tolist()) & set(b[b >= 0].tolist())) for a, b in zip(gi, oi))
     assert hits / max(1, int((oi >= 0).sum())) >= 0.995
     G.close()
+
+
+def test_trim_pool_then_rebuild(hf):
+    """Memory returned by hf_trim_pool is taken again by the next build; the
+    results do not change."""
+    x = S.unit_gaussian(2000, 16, seed=3)
+    G = hf.build(cuda(x), T=2, bits=8)
+    gi, gd = G.knn_graph(5, 4)
+    G.close()
+    hf.trim_pool()
+    G = hf.build(cuda(x), T=2, bits=8)
+    gi2, gd2 = G.knn_graph(5, 4)
+    torch.cuda.synchronize()
+    assert torch.equal(gi, gi2) and torch.equal(gd, gd2)
+    G.close()
