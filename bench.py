@@ -11,10 +11,16 @@ mixture with Zipf(1.1) weights, T trees, b = 8, window w, k = 15; plus 10,000
 mixture queries with N(0, 0.05^2) noise. The paper measured on GOOAQ
 (3M x 384); these seeded synthetic inputs stand in for it.
 
+The default form is the tensor mode: window distances as BF16 Gram tiles on
+the tensor cores (tcgen05) keeping k + 1 candidates per point, then an exact
+float32 re-rank; `--mode plain` runs the all-float32 window kernel instead
+(two plain steps are also timed beside the default, for comparison).
+
 Prints one JSON line (rank 0). `value` = points / s of the device-resident
 step; `e2e` = the same through the C ABI with pinned host buffers (copies in
-the timed region); `roofline` for the window kernel (the dominant one);
-`cpu_baseline` = the CPU oracle on a bounded sample.
+the timed region); `roofline` for the dominant kernel (the Gram kernel in
+tensor mode, the window kernel in plain mode); `cpu_baseline` = the CPU oracle
+on a bounded sample.
 
 --impl reference times the CPU oracle itself (the only reference this
 project has: the paper ships no code) on a bounded sample per step.
@@ -38,10 +44,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "kNN-graph points/s at recall@k>=0.8; Hilbert-sort Mkeys/s; % HBM/TC roofline"
 
-# Window-kernel DRAM traffic from one ncu capture of a 1M-point launch (bytes
-# per point, scaled by n here) and the window.cu source it was taken on; the
-# figure is dropped (null) once the source differs.
-WINDOW_TRAFFIC = {"bytes_per_point": 1915, "source_sha": "c47a6c4277b03192"}
+# DRAM traffic of the dominant kernels from one ncu capture of a 1M-point
+# launch (bytes per point, scaled by n here) and the source file it was taken
+# on; a figure is dropped (null) once its source differs.
+WINDOW_TRAFFIC = {"bytes_per_point": 1915, "source_sha": "c47a6c4277b03192", "file": "window.cu"}
+GRAM_TRAFFIC = {"bytes_per_point": None, "source_sha": "", "file": "gram.cu"}
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
@@ -65,8 +72,9 @@ def args():
     p.add_argument("--recall-sample", type=int, default=2000)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=20000)
-    p.add_argument("--mode", default="plain", choices=["plain", "tensor"])
+    p.add_argument("--cpu-sample", type=int, default=60000)
+    p.add_argument("--mode", default="tensor", choices=["plain", "tensor"])
+    p.add_argument("--plain-steps", type=int, default=2, help="plain-mode steps timed beside tensor mode")
     p.add_argument("--tensor-slack", type=int, default=-1)
     return p.parse_args()
 
@@ -234,21 +242,39 @@ def run_ours(a):
         ms_step = float(t.item())
 
     ph = {kk: statistics.mean(p[kk] for p in phases) for kk in phases[0]}
-    window_ms = ph["window_merge"] / T  # per launch (list init included, < 1%)
-    pairs = n * w - w * (w + 1) // 2
-    flops = 3.0 * d * pairs
-    achieved = flops / (window_ms * 1e-3) / 1e12
-    peak = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 * 1.5 / 1e12
-    traffic = None
-    src = open(os.path.join(ROOT, "paper_2508_21682_gb300", "csrc", "window.cu"), "rb").read()
-    if WINDOW_TRAFFIC["bytes_per_point"] and WINDOW_TRAFFIC["source_sha"] == hashlib.sha256(src).hexdigest()[:16]:
-        traffic = WINDOW_TRAFFIC["bytes_per_point"] * n
+    launch_ms = ph["window_merge"] / T  # per launch (list init included, < 1%)
+    if a.mode == "tensor":
+        roof = gram_roofline(a, launch_ms)
+    else:
+        roof = window_roofline(a, launch_ms)
+
+    # plain float32 mode beside it (outside the timed region)
+    plain = None
+    if a.mode == "tensor" and a.plain_steps > 0:
+        saved = a.mode
+        a.mode = "plain"
+        step()
+        torch.cuda.synchronize()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.plain_steps)]
+        for e0, e1 in pe:
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        a.mode = saved
+        pms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in pe)
+        plain = {"ms_per_step": pms, "value": n / (pms * 1e-3), "unit": "points/s"}
+        gi_plain = gi.cpu().numpy()
 
     # recall on a seeded sample (outside the timed region)
     rng = np.random.default_rng(4)
     rows = np.sort(rng.choice(n, size=min(a.recall_sample, n), replace=False))
     rows_t = torch.from_numpy(rows).to(dev)
     ex = exact_knn_gpu(xd, xd[rows_t], k, exclude=rows_t)
+    if plain is not None:
+        plain["recall_at_k"] = recall(gi_plain[rows], ex)
+        step()  # the default mode's graph again for its own recall
+        torch.cuda.synchronize()
     rec = recall(gi.cpu().numpy()[rows], ex)
     qs = min(500, a.nq)
     exq = exact_knn_gpu(xd, qd[:qs], k)
@@ -299,7 +325,7 @@ def run_ours(a):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "bf16+f32" if a.mode == "tensor" else "f32",
             "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
             "config": {"workload": workload_name(a), "n": n, "d": d, "T": T, "bits": a.bits, "w": w, "k": k,
                        "queries": a.nq, "mode": "plain f32" if a.mode == "plain" else "bf16 tcgen05 Gram + f32 re-rank",
@@ -310,10 +336,8 @@ def run_ours(a):
             "search_recall_at_k": rec_q,
             "hilbert_sort_mkeys_s": n * T / (hs_ms * 1e-3) / 1e6,
             "phase_ms": ph,
-            "roofline": {"bound": "alu", "kernel": "window_kernel (A5+A6, plain f32)",
-                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": traffic,
-                         "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz, 3 flops per FADD+FFMA pair"},
+            "roofline": roof,
+            "plain_f32": plain,
             "e2e": {"value": ws * n / (e2e_step * 1e-3), "unit": "points/s",
                     "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
@@ -325,6 +349,52 @@ def run_ours(a):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def traffic_per_launch(entry, n):
+    src = open(os.path.join(ROOT, "paper_2508_21682_gb300", "csrc", entry["file"]), "rb").read()
+    if entry["bytes_per_point"] and entry["source_sha"] == hashlib.sha256(src).hexdigest()[:16]:
+        return entry["bytes_per_point"] * n
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "of measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def gram_roofline(a, launch_ms):
+    """HBM roofline of one Gram launch (one tree): algorithmic bytes per point
+    = the BF16 row (2 ceil64(d)), the point's list read and written (2 KP x 8
+    bytes, KP = list slots), its id and norm (8 bytes)."""
+    dp = -(-a.d // 64) * 64
+    kp = 16 if a.k + 1 <= 16 else (32 if a.k + 1 <= 32 else 64)
+    per_point = 2 * dp + 2 * kp * 8 + 8
+    bytes_launch = per_point * a.n
+    peaks, src = measured_peaks()
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "kernel": "gram_window_kernel (A5+A6, BF16 tcgen05 Gram tiles + band top-k merge)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_per_launch(GRAM_TRAFFIC, a.n),
+            "bytes_per_launch": bytes_launch, "bytes_per_point": per_point, "launch_ms": launch_ms,
+            "peak_note": f"hbm_gbs {src} (MEASURED_PEAKS.json)"}
+
+
+def window_roofline(a, launch_ms):
+    """ALU roofline of one plain window launch: 3 flops per (pair, coordinate)."""
+    n, w, d = a.n, a.w, a.d
+    pairs = n * w - w * (w + 1) // 2
+    flops = 3.0 * d * pairs
+    achieved = flops / (launch_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 * 1.5 / 1e12
+    return {"bound": "alu", "kernel": "window_kernel (A5+A6, plain f32)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_per_launch(WINDOW_TRAFFIC, n), "launch_ms": launch_ms,
+            "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz, 3 flops per FADD+FFMA pair"}
 
 
 def oracle_sample(a, n_s, T_s, seed_offset=0):

@@ -209,8 +209,10 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
 
 /*
  * hf_get_timings -- milliseconds of the last calls' phases, in this order:
- * [0] quantize, [1] keys, [2] sort, [3] tie fix-up, [4] window+merge,
- * [5] search, [6] keys+sort launches count (as float). Writes min(cap, 7).
+ * [0] quantize, [1] keys, [2] sort (with the small-run fix-up), [3] big-run
+ * fix-up, [4] window distances + merge (all trees; the Gram kernels in mode
+ * 1), [5] search, [6] number of kernel launches of the last build (as a
+ * float), [7] re-rank (mode 1). Writes min(cap, 8).
  */
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
 

@@ -233,9 +233,9 @@ class Forest:
         _check(lib().hf_set_option(self._h, key.encode(), value), "hf_set_option")
 
     def timings(self):
-        t = np.zeros(7, np.float32)
-        lib().hf_get_timings(self._h, t.ctypes.data, 7)
-        names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches"]
+        t = np.zeros(8, np.float32)
+        lib().hf_get_timings(self._h, t.ctypes.data, 8)
+        names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches", "rerank"]
         return dict(zip(names, t.tolist()))
 
     # ---- inspection --------------------------------------------------------

@@ -463,7 +463,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
 
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap) {
   if (!f || !out_ms || cap < 0) return HF_EINVAL;
-  for (int i = 0; i < cap && i < 7; ++i) out_ms[i] = f->timings[i];
+  for (int i = 0; i < cap && i < 8; ++i) out_ms[i] = f->timings[i];
   return HF_OK;
 }
 
@@ -511,9 +511,11 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
     else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }
-  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, f->sigma, kp, li, ldd, s);
   cudaEvent_t a1 = tm.mark();
+  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, f->sigma, kp, li, ldd, s);
+  cudaEvent_t a2 = tm.mark();
   tm.span(4, a0, a1);
+  tm.span(7, a1, a2);
   // first k of kp columns into the caller's buffers (device or host)
   if (rc == HF_OK)
     rc = map_cuda(cudaMemcpy2DAsync(out_idx, (size_t)k * 4, li, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
@@ -523,7 +525,7 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
                                     cudaMemcpyDefault, s));
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
-  if (rc == HF_OK) tm.collect({4});
+  if (rc == HF_OK) tm.collect({4, 7});
   dfree(li, s);
   dfree(ldd, s);
   return rc;
