@@ -113,6 +113,7 @@ int finish(hf_forest* f, cudaStream_t s) {
 
 void free_build_scratch(hf_forest* f, cudaStream_t s) {
   dfree(f->pk, s);
+  dfree(f->p0t, s);
   dfree(f->sort.keys_a, s);
   dfree(f->sort.keys_b, s);
   dfree(f->sort.vals_a, s);
@@ -345,6 +346,8 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   chk(dalloc(&f->sigma, (size_t)T * n, s));
   chk(dalloc(&f->err, 1, s));
   chk(dalloc(&f->pk, (size_t)TB * f->K2 * n, s));
+  const bool sliced = prefix_top_path(d, f->K2, f->L);
+  if (sliced) chk(dalloc(&f->p0t, (size_t)((n + 31) / 32) * d, s));
   chk(dalloc(&f->sort.keys_a, (size_t)TB * n, s));
   chk(dalloc(&f->sort.keys_b, (size_t)TB * n, s));
   chk(dalloc(&f->sort.vals_a, (size_t)TB * n, s));
@@ -383,6 +386,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   cudaEvent_t a0 = tm.mark();
   launch_range(f->x, n, d, f->lo, f->scale, bits, f->err, rscratch, rbytes, s);
   launch_quantize_planes(f->x, n, d, f->lo, f->scale, bits, f->planes, f->err, s);
+  if (sliced) launch_plane0_slice(f->planes, n, d, f->p0t, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(0, a0, a1);
   for (int t0 = 0; t0 < T && rc == HF_OK; t0 += TB) {
@@ -390,7 +394,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     cudaEvent_t k0 = tm.mark();
     for (int j = 0; j < tb; ++j) {
       const int t = t0 + j;
-      launch_prefix_keys(f->planes, n, d, bits, f->K2, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32,
+      launch_prefix_keys(f->planes, f->p0t, n, d, bits, f->K2, f->L, f->pi + (size_t)t * d, f->rbits + (size_t)t * W32,
                          f->pk + (size_t)j * f->K2 * n, s);
     }
     cudaEvent_t k1 = tm.mark();

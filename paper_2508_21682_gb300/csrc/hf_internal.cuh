@@ -66,6 +66,7 @@ struct hf_forest {
   float* xnrm = nullptr;
 
   uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
+  uint32_t* p0t = nullptr;    // [ceil(n/32)][d] bit-sliced plane 0 (scratch, top-level prefix path)
   int TB = 1;                 // trees keyed and sorted together
   SortScratch sort;
   TieScratch tie;
@@ -96,7 +97,11 @@ void launch_planes_to_codes(const uint32_t* planes, int64_t n, int d, int bits, 
                             cudaStream_t s);
 
 // keys.cu
-void launch_prefix_keys(const uint32_t* planes, int64_t n, int d, int bits, int K, int L,
+bool prefix_top_path(int d, int K, int L);  // prefix words from plane 0 alone
+// plane 0 in bit-sliced form: p0t[g][c] bit j = top bit of coordinate c of point 32g + j
+void launch_plane0_slice(const uint32_t* planes, int64_t n, int d, uint32_t* p0t, cudaStream_t s);
+// p0t: the bit-sliced plane 0 (used on the top-level path), or null
+void launch_prefix_keys(const uint32_t* planes, const uint32_t* p0t, int64_t n, int d, int bits, int K, int L,
                         const int32_t* pi, const uint32_t* rbits, uint64_t* pk, cudaStream_t s);
 void launch_full_keys_planes(const uint32_t* planes, int64_t n, int d, int bits, int W,
                              const int32_t* pi, const uint32_t* rbits, uint64_t* out,

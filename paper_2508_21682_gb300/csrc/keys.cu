@@ -9,9 +9,12 @@
 // Two prefix paths:
 //  * top-level path (the first 64K key bits all lie in bit level 0, i.e.
 //    d >= 64K): those bits are the running XOR of the permuted, reflected top
-//    bits of coordinates 0 .. 64K-1. Each block stages the plane-0 rows of its
-//    points in shared memory and every thread gathers, XOR-scans and packs its
-//    point's bits word by word.
+//    bits of coordinates 0 .. 64K-1. It works on plane 0 in bit-sliced form
+//    (one 32-bit word per group of 32 points and coordinate, made once per
+//    build): a warp takes one group, lane l reads the word of permuted
+//    coordinate 32h + l, an XOR scan across the lanes gives key bits
+//    32h .. 32h+31 of all 32 points at once, and a bit-matrix transpose across
+//    the warp hands each point its 32 key bits.
 //  * general path: each thread forms the top L bits of all d coordinates in
 //    shared memory and runs the transform with L levels.
 #include <cuda_runtime.h>
@@ -21,65 +24,78 @@
 
 namespace {
 
-constexpr int TOP_THREADS = 128;
-
-// Running XOR from the most significant bit down: bit j of the result is the
-// XOR of bits 31..j of v.
-__device__ __forceinline__ uint32_t xor_scan_msb(uint32_t v) {
-  v ^= v >> 1;
-  v ^= v >> 2;
-  v ^= v >> 4;
-  v ^= v >> 8;
-  v ^= v >> 16;
-  return v;
+// 32 x 32 bit-matrix transpose across the warp: lane l holds row l (bit j =
+// entry (l, j)); afterwards lane j holds column j (bit l = entry (l, j)).
+// Stage s swaps the off-diagonal s x s blocks between lanes l and l ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    uint32_t mlo = 0;  // bit positions p with (p & s) == 0
+#pragma unroll
+    for (int p = 0; p < 32; ++p)
+      if (!(p & s)) mlo |= 1u << p;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~mlo) | ((y & ~mlo) >> s)) : ((x & mlo) | ((y & mlo) << s));
+  }
+  return x;
 }
 
-__global__ void __launch_bounds__(TOP_THREADS)
-prefix_top_kernel(const uint32_t* __restrict__ plane0, int64_t n, int d, int W32, int K,
-                  const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
-                  uint64_t* __restrict__ pk) {
-  extern __shared__ uint32_t sm[];
-  const int nbits = 64 * K;                 // bits needed, all from plane 0
-  int32_t* s_pi = reinterpret_cast<int32_t*>(sm);  // [nbits]
-  uint32_t* s_r = sm + nbits;                      // [nbits / 32]
-  uint32_t* s_rows = s_r + nbits / 32;             // [TOP_THREADS][W32 + 1]
-  const int stride = W32 + 1;
+// Bit-sliced plane 0: p0t[g][c] bit j = top bit of coordinate c of point
+// 32g + j (0 past the last point). One warp per (group, plane word): lane j
+// reads point 32g + j's word m, the transpose leaves coordinate 32m + c's word
+// in lane c.
+__global__ void plane0_slice_kernel(const uint32_t* __restrict__ plane0, int64_t n, int d, int W32,
+                                    uint32_t* __restrict__ p0t) {
+  const int lane = threadIdx.x & 31;
+  const int64_t G = (n + 31) / 32;
+  const int64_t tasks = G * W32;
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < tasks;
+       e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t g = e / W32;
+    const int m = (int)(e - g * W32);
+    const int64_t p = g * 32 + lane;
+    uint32_t x = p < n ? __ldg(plane0 + (size_t)p * W32 + m) : 0u;
+    x = warp_transpose32(x, lane);
+    const int c = m * 32 + lane;
+    if (c < d) p0t[(size_t)g * d + c] = x;
+  }
+}
 
-  for (int i = threadIdx.x; i < nbits; i += blockDim.x) s_pi[i] = pi[i];
-  for (int i = threadIdx.x; i < nbits / 32; i += blockDim.x) {
-    // reflection bits of permuted axes 32i .. 32i+31, reordered MSB-first so
-    // that bit 31 belongs to axis 32i
-    s_r[i] = __brev(rbits[i]);
-  }
-  const int64_t p0 = (int64_t)blockIdx.x * TOP_THREADS;
-  const int rows = (int)((n - p0) < TOP_THREADS ? (n - p0) : TOP_THREADS);
-  for (int e = threadIdx.x; e < rows * W32; e += blockDim.x) {
-    const int r = e / W32, m = e - r * W32;
-    s_rows[r * stride + m] = __ldg(plane0 + (p0 + r) * W32 + m);
-  }
-  __syncthreads();
-  if ((int)threadIdx.x >= rows) return;
-  const uint32_t* row = s_rows + threadIdx.x * stride;
-  uint32_t carry = 0;  // parity of all earlier bits
-  const int64_t p = p0 + threadIdx.x;
-  for (int w = 0; w < K; ++w) {
-    uint32_t half[2];
+// Top-level prefix words 0 .. K-1 from the bit-sliced plane 0, one warp per
+// group of 32 points. For half-word h, lane l takes key bit i = 32h + l: the
+// word of permuted axis pi[i] (inverted when the axis is reflected) holds
+// that bit's input for all 32 points; an inclusive XOR scan over the lanes
+// plus the running carry of the earlier halves gives key bit i for all 32
+// points, and the transpose (bit-reversed: the key is packed most significant
+// bit first) gives point j its 32 bits 32h .. 32h+31.
+__global__ void prefix_sliced_kernel(const uint32_t* __restrict__ p0t, int64_t n, int d, int K,
+                                     const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
+                                     uint64_t* __restrict__ pk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t G = (n + 31) / 32;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint32_t* row = p0t + (size_t)g * d;
+    const int64_t p = g * 32 + lane;
+    uint32_t carry = 0, hi = 0;
+    for (int h = 0; h < 2 * K; ++h) {
+      const int i = 32 * h + lane;
+      uint32_t v = __ldg(row + __ldg(pi + i));
+      if ((__ldg(rbits + h) >> lane) & 1u) v = ~v;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int base = w * 64 + h * 32;
-      uint32_t v = 0;
-#pragma unroll 8
-      for (int j = 0; j < 32; ++j) {
-        const int c = s_pi[base + j];
-        v = (v << 1) | ((row[c >> 5] >> (c & 31)) & 1u);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v ^= t;
       }
-      v ^= s_r[base >> 5];
-      v = xor_scan_msb(v);
-      if (carry) v = ~v;
-      carry = v & 1u;
-      half[h] = v;
+      v ^= carry;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+      const uint32_t half = __brev(warp_transpose32(v, lane));
+      if (h & 1) {
+        if (p < n) pk[(size_t)(h >> 1) * n + p] = ((uint64_t)hi << 32) | half;
+      } else {
+        hi = half;
+      }
     }
-    pk[(size_t)w * n + p] = ((uint64_t)half[0] << 32) | half[1];
   }
 }
 
@@ -135,14 +151,22 @@ void set_smem(const void* fn, size_t bytes) {
 
 }  // namespace
 
-void launch_prefix_keys(const uint32_t* planes, int64_t n, int d, int bits, int K, int L,
+bool prefix_top_path(int d, int K, int L) { return L == 1 && d >= 64 * K; }
+
+void launch_plane0_slice(const uint32_t* planes, int64_t n, int d, uint32_t* p0t, cudaStream_t s) {
+  const int W32 = (d + 31) / 32;
+  const int64_t tasks = (n + 31) / 32 * W32;
+  plane0_slice_kernel<<<hf_blocks(tasks * 32, 256, 152 * 16), 256, 0, s>>>(planes, n, d, W32, p0t);
+  hf_after_launch("plane0_slice_kernel", s);
+}
+
+void launch_prefix_keys(const uint32_t* planes, const uint32_t* p0t, int64_t n, int d, int bits, int K, int L,
                         const int32_t* pi, const uint32_t* rbits, uint64_t* pk, cudaStream_t s) {
   const int W32 = (d + 31) / 32;
-  if (L == 1 && d >= 64 * K) {
-    const size_t smem = (size_t)(64 * K + 2 * K + TOP_THREADS * (W32 + 1)) * sizeof(uint32_t);
-    set_smem((const void*)prefix_top_kernel, smem);
-    prefix_top_kernel<<<hf_blocks(n, TOP_THREADS), TOP_THREADS, smem, s>>>(planes, n, d, W32, K, pi,
-                                                                           rbits, pk); hf_after_launch("prefix_top_kernel", s);
+  if (prefix_top_path(d, K, L) && p0t) {
+    const int64_t G = (n + 31) / 32;
+    prefix_sliced_kernel<<<hf_blocks(G * 32, 256, 152 * 16), 256, 0, s>>>(p0t, n, d, K, pi, rbits, pk);
+    hf_after_launch("prefix_sliced_kernel", s);
     return;
   }
   const int t = threads_for_bytes_per_thread(d);
