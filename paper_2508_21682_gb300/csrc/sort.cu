@@ -135,7 +135,7 @@ struct PassArgs {
 // GATHER: the key of the element at position e is gather_src[vals_in[e]]
 // (the next prefix word, fetched in the current order).
 template <bool GATHER>
-__global__ void __launch_bounds__(NT) onesweep_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   PassSmem& S = *reinterpret_cast<PassSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
