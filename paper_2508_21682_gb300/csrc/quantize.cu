@@ -106,12 +106,26 @@ __device__ __forceinline__ uint32_t quantize_one(float x, float lo, float scale,
   return (uint32_t)cl;
 }
 
+// 8 x 8 bit-matrix transpose of a 64-bit word: bit c of byte u moves to
+// bit u of byte c (delta swaps of 7, 14 and 28 positions).
+__device__ __forceinline__ uint64_t transpose8x8(uint64_t x) {
+  uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x = x ^ t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x = x ^ t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x = x ^ t ^ (t << 28);
+  return x;
+}
+
 // One warp per point. The warp first copies the point's row into its
 // shared-memory slot (16-byte loads when rows are 16-byte aligned, all issued
-// before any is used), then quantizes 32 coordinates per step: lane j takes
-// coordinate 32m + j and eight ballots over the code (aligned to 8 bits) give
-// the plane words; lane l keeps plane l's word in shared memory. The point's
-// plane rows (W32 words each) are then written out contiguously.
+// before any is used). Lane j then takes groups of 8 consecutive coordinates
+// (8g .. 8g+7, g = j, j + 32, ...): it quantizes them, packs the 8 codes
+// (aligned to 8 bits) into one 64-bit word and transposes it as an 8 x 8 bit
+// matrix, so that byte 7 - l holds bit plane l of the 8 coordinates: byte g
+// of the point's plane-l row. The plane rows (W32 words each) are collected
+// in shared memory and written out contiguously.
 constexpr int QP_THREADS = 256;
 
 __global__ void __launch_bounds__(QP_THREADS)
@@ -119,13 +133,14 @@ quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, c
                        const float* __restrict__ scale, int bits, int vec4, uint32_t* __restrict__ planes) {
   extern __shared__ __align__(16) float qsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int dpad = (d + 3) & ~3;
-  const int wstride = (dpad + bits * W32 + 3) & ~3;  // floats per warp, keeps 16-byte alignment
+  const int rowf = 32 * W32;                       // staged floats (>= d)
+  const int wstride = (rowf + bits * W32 + 3) & ~3;  // floats per warp, keeps 16-byte alignment
   float* row_s = qsm + (size_t)wib * wstride;
-  uint32_t* word_s = reinterpret_cast<uint32_t*>(row_s + dpad);  // [bits][W32]
+  uint32_t* word_s = reinterpret_cast<uint32_t*>(row_s + rowf);  // [bits][W32]
+  uint8_t* byte_s = reinterpret_cast<uint8_t*>(word_s);          // [bits][4 W32]
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4;
+  const int groups = 4 * W32;
   for (int64_t i = warp; i < n; i += nwarps) {
     const float* row = x + (size_t)i * d;
     if (vec4) {
@@ -135,21 +150,33 @@ quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, c
       for (int c = lane; c < d; c += 32) row_s[c] = __ldg(row + c);
     }
     __syncwarp();
-    for (int m = 0; m < W32; ++m) {
-      const int c = m * 32 + lane;
-      uint32_t code = 0;
-      if (c < d) code = quantize_one(row_s[c], __ldg(lo + c), __ldg(scale + c), bits);
-      // plane l is bit 7 - l of the 8-bit-aligned code (words past `bits`
-      // are unused); lane l picks word l through a select tree on its lane bits
-      const uint32_t c8 = code << (8 - bits);
-      uint32_t w[8];
+    for (int g = lane; g < groups; g += 32) {
+      const int c0 = 8 * g;
+      uint32_t w0 = 0, w1 = 0;  // codes of coordinates c0 .. c0+3 and c0+4 .. c0+7, one per byte
+      if (vec4 && c0 + 8 <= d) {
+        const float4 xa = *reinterpret_cast<const float4*>(row_s + c0);
+        const float4 xb = *reinterpret_cast<const float4*>(row_s + c0 + 4);
+        const float4 la = __ldg(reinterpret_cast<const float4*>(lo + c0));
+        const float4 lb = __ldg(reinterpret_cast<const float4*>(lo + c0 + 4));
+        const float4 sa = __ldg(reinterpret_cast<const float4*>(scale + c0));
+        const float4 sb = __ldg(reinterpret_cast<const float4*>(scale + c0 + 4));
+        w0 = quantize_one(xa.x, la.x, sa.x, bits) | (quantize_one(xa.y, la.y, sa.y, bits) << 8) |
+             (quantize_one(xa.z, la.z, sa.z, bits) << 16) | (quantize_one(xa.w, la.w, sa.w, bits) << 24);
+        w1 = quantize_one(xb.x, lb.x, sb.x, bits) | (quantize_one(xb.y, lb.y, sb.y, bits) << 8) |
+             (quantize_one(xb.z, lb.z, sb.z, bits) << 16) | (quantize_one(xb.w, lb.w, sb.w, bits) << 24);
+      } else {
 #pragma unroll
-      for (int l = 0; l < 8; ++l) w[l] = __ballot_sync(0xffffffffu, c8 & (0x80u >> l));
-      const uint32_t s01 = b0 ? w[1] : w[0], s23 = b0 ? w[3] : w[2];
-      const uint32_t s45 = b0 ? w[5] : w[4], s67 = b0 ? w[7] : w[6];
-      const uint32_t s03 = b1 ? s23 : s01, s47 = b1 ? s67 : s45;
-      const uint32_t mine = b2 ? s47 : s03;
-      if (lane < bits) word_s[lane * W32 + m] = mine;
+        for (int u = 0; u < 8; ++u) {
+          const int c = c0 + u;
+          const uint32_t code = c < d ? quantize_one(row_s[c], __ldg(lo + c), __ldg(scale + c), bits) : 0u;
+          if (u < 4) w0 |= code << (8 * u);
+          else w1 |= code << (8 * (u - 4));
+        }
+      }
+      // align every code to 8 bits (the shift stays inside each byte)
+      const uint64_t packed = ((uint64_t)w1 << 32 | w0) << (8 - bits);
+      const uint64_t tr = transpose8x8(packed);
+      for (int l = 0; l < bits; ++l) byte_s[l * groups + g] = (uint8_t)(tr >> (8 * (7 - l)));
     }
     __syncwarp();
     for (int l = 0; l < bits; ++l)
@@ -231,7 +258,7 @@ void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, c
   (void)err;
   const int W32 = (d + 31) / 32;
   const int vec4 = d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
-  const size_t smem = (size_t)(QP_THREADS / 32) * ((((d + 3) & ~3) + bits * W32 + 3) & ~3) * 4;
+  const size_t smem = (size_t)(QP_THREADS / 32) * ((32 * W32 + bits * W32 + 3) & ~3) * 4;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute((const void*)quantize_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   quantize_planes_kernel<<<hf_blocks(n * 32, QP_THREADS, 152 * 16), QP_THREADS, smem, s>>>(x, n, d, W32, lo, scale,
