@@ -301,10 +301,14 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   {
     const int64_t need = ((int64_t)64 * f->K + d - 1) / d;
     f->L = (int)(need < bits ? need : bits);
-    // words past the sorted prefix that come from the same L top levels are
-    // computed with it (up to four): they settle equal prefixes cheaply
+    // With L > 1, words past the sorted prefix that come from the same L top
+    // levels are computed with it (up to four): they settle equal prefixes
+    // cheaply. On the top-level path (L = 1) the fix-up forms them itself
+    // with ballots for the tied points only, which costs less than computing
+    // them for every point.
     f->K2 = f->K;
-    while (f->K2 < f->W && f->K2 < f->K + 4 && (int64_t)64 * (f->K2 + 1) <= (int64_t)d * f->L) ++f->K2;
+    if (f->L > 1)
+      while (f->K2 < f->W && f->K2 < f->K + 4 && (int64_t)64 * (f->K2 + 1) <= (int64_t)d * f->L) ++f->K2;
   }
   cudaGetDevice(&f->device);
 

@@ -342,12 +342,24 @@ __device__ __forceinline__ bool full_less(const uint64_t* a, uint32_t ia, const 
   return ia < ib;
 }
 
+// Running XOR from the most significant bit down: bit j of the result is the
+// XOR of bits 31..j of v.
+__device__ __forceinline__ uint32_t xor_scan_msb(uint32_t v) {
+  v ^= v >> 1;
+  v ^= v >> 2;
+  v ^= v >> 4;
+  v ^= v >> 8;
+  v ^= v >> 16;
+  return v;
+}
+
 // One block per small run (grid-stride over runs). The run's prefixes (words
 // 0..K-1) are equal, so the order inside it is decided by the following key
 // words K..K2-1. When the key kernel computed them (kpre > K) they are read
 // from pkx[w][point]; otherwise they are computed here: they lie in the top
 // Lf bit levels, and the top Lf levels of a key equal the Lf-bit key of the
-// coordinates' top Lf bits, so they cost a transform with Lf levels only.
+// coordinates' top Lf bits, so they cost a transform with Lf levels only
+// (with Lf = 1 a running XOR, which a warp forms with ballots).
 // Each point's rank = number of run members below it by (words K..K2-1,
 // index). Only if two members also tie on those words does the block compute
 // full keys (into its own slice of global scratch) and rank by (full key,
@@ -373,16 +385,47 @@ __global__ void tie_small_kernel(const uint32_t* __restrict__ planes, int64_t n,
     const uint2 run = runs[r];
     const int len = (int)run.y;  // <= cap by construction
     if (threadIdx.x == 0) s_tie = 0;
-    for (int e = threadIdx.x; e < len; e += blockDim.x) {
-      const uint32_t p = sigma[run.x + e];
-      pt[e] = p;
-      if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
-      if (kpre > K) {
-        for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = __ldg(pkx + (size_t)(K + w) * n + p);
-      } else {
-        hf_load_coords_planes(planes, n, d, W32, Lf, pi, rbits, p, Y);
-        hf_skilling(Y, d, Lf);
-        for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = hf_pack_word(Y, d, Lf, K + w);
+    if (kpre <= K && Lf == 1) {
+      // Words K .. K2-1 lie in the top bit level: one warp per member forms
+      // them with ballots over the permuted, reflected top bits (plane 0),
+      // carrying the parity of the first 64K bits.
+      const int lane = threadIdx.x & 31;
+      for (int e = threadIdx.x >> 5; e < len; e += blockDim.x >> 5) {
+        const uint32_t p = sigma[run.x + e];
+        if (lane == 0) pt[e] = p;
+        if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
+        const uint32_t* row = planes + (size_t)p * W32;
+        uint32_t carry = 0, hi = 0;
+        for (int h = 0; h < 2 * K2; ++h) {
+          const int c = __ldg(pi + 32 * h + lane);
+          const uint32_t bit = ((__ldg(row + (c >> 5)) >> (c & 31)) ^ (__ldg(rbits + h) >> lane)) & 1u;
+          const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+          if (h < 2 * K) {
+            carry ^= __popc(bal) & 1u;
+            continue;
+          }
+          uint32_t v = xor_scan_msb(__brev(bal));
+          if (carry) v = ~v;
+          carry = v & 1u;
+          if (h & 1) {
+            if (lane == 0) tk[(size_t)e * KT + (h >> 1) - K] = ((uint64_t)hi << 32) | v;
+          } else {
+            hi = v;
+          }
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const uint32_t p = sigma[run.x + e];
+        pt[e] = p;
+        if (p >= (uint64_t)n) continue;  // cannot happen for a valid order
+        if (kpre > K) {
+          for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = __ldg(pkx + (size_t)(K + w) * n + p);
+        } else {
+          hf_load_coords_planes(planes, n, d, W32, Lf, pi, rbits, p, Y);
+          hf_skilling(Y, d, Lf);
+          for (int w = 0; w < KT; ++w) tk[(size_t)e * KT + w] = hf_pack_word(Y, d, Lf, K + w);
+        }
       }
     }
     __syncthreads();
