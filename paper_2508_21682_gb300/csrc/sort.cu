@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
   for (int j = 0; j < IPT; ++j) {
     const int64_t e = base + warp * 32 * IPT + j * 32 + lane;
     if (e < n) {
-      v[j] = vals_in ? __ldg(vals_in + e) : (uint32_t)e;
+      // read once per pass: streaming loads leave L2 to the pass's output
+      v[j] = vals_in ? __ldcs(vals_in + e) : (uint32_t)e;
       if (GATHER) {
         // values are point indices < n unless an earlier pass gave up its
         // look-back (error word set); never read outside the source then
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
         }
         k[j] = __ldg(gather_src + v[j]);
       } else {
-        k[j] = __ldg(keys_in + e);
+        k[j] = __ldcs(reinterpret_cast<const unsigned long long*>(keys_in) + e);
       }
       dg[j] = (uint32_t)(k[j] >> shift) & 255u;
     } else {
@@ -209,16 +210,48 @@ __global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
     cnt += c;
   }
 
+  // The tile's counts are published first (its successors can use them at
+  // once); the tile-local offsets and the scatter into shared memory run
+  // before this tile waits for its own predecessors.
+  uint32_t* st = status + tile * 256 + dgt;
+  st_relaxed(st, (tile == 0 ? FLAG_PRE : FLAG_AGG) | cnt);
+
+  // Tile-local exclusive scan of the digit counts (warp scans + warp totals),
+  // folded into the per-warp offsets.
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) S.scan[warp] = incl;
+  __syncthreads();
+  uint32_t woff = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w)
+    if (w < warp) woff += S.scan[w];
+  const uint32_t tstart = woff + incl - cnt;
+  S.tile_start[dgt] = tstart;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) S.whist[w][dgt] += tstart;
+  __syncthreads();
+
+  // Scatter into shared memory in digit order.
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    if (dg[j] < 256u) {
+      const uint32_t lp = S.whist[warp][dg[j]] + rk[j];
+      S.keys[lp] = k[j];
+      S.vals[lp] = v[j];
+    }
+  }
+
   // Decoupled look-back for this digit. LB predecessor status words are read
   // at once (independent loads, one round trip), then consumed in order:
   // aggregates are added until an inclusive prefix ends the walk; a word that
   // is not ready yet is re-read from there on the next round.
-  uint32_t* st = status + tile * 256 + dgt;
   uint32_t excl = 0;
-  if (tile == 0) {
-    st_relaxed(st, FLAG_PRE | cnt);
-  } else {
-    st_relaxed(st, FLAG_AGG | cnt);
+  if (tile > 0) {
     int64_t pred = tile - 1;
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
@@ -254,34 +287,10 @@ __global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
     }
     st_relaxed(st, FLAG_PRE | ((excl + cnt) & VAL_MASK));
   }
-
-  // Tile-local exclusive scan of the digit counts (warp scans + warp totals).
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) S.scan[warp] = incl;
-  __syncthreads();
-  uint32_t woff = 0;
-#pragma unroll
-  for (int w = 0; w < WARPS; ++w)
-    if (w < warp) woff += S.scan[w];
-  S.tile_start[dgt] = woff + incl - cnt;
   S.gbase[dgt] = goff[dgt] + excl;
   __syncthreads();
 
-  // Scatter into shared memory in digit order, then write out coalesced.
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    if (dg[j] < 256u) {
-      const uint32_t lp = S.tile_start[dg[j]] + S.whist[warp][dg[j]] + rk[j];
-      S.keys[lp] = k[j];
-      S.vals[lp] = v[j];
-    }
-  }
-  __syncthreads();
+  // Write out coalesced (runs of equal digits go to consecutive positions).
   const int valid = (int)(n - base < TILE ? n - base : TILE);
   for (int e = tid; e < valid; e += NT) {
     const uint64_t key = S.keys[e];
