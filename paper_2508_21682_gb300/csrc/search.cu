@@ -330,19 +330,28 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
         for (int u = 0; u < 32; ++u) part[u] = 0.f;
         for (int m = 4 * lane; m < a.d; m += 128) {
           const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + m));
+          // 8 candidate rows per group: all 8 loads are issued before any is
+          // used (an empty slot reads the query's own row; its result is
+          // discarded)
 #pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            const uint32_t p = cpid[u];
-            if (p != 0xffffffffu) {
-              const float4 xa = __ldg(reinterpret_cast<const float4*>(a.x + (size_t)p * a.d + m));
-              float e = qa.x - xa.x;
-              float acc = fmaf(e, e, part[u]);
-              e = qa.y - xa.y;
+          for (int u0 = 0; u0 < 32; u0 += 8) {
+            float4 xb[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const uint32_t p = cpid[u0 + u];
+              const float* row = p != 0xffffffffu ? a.x + (size_t)p * a.d : qv;
+              xb[u] = __ldg(reinterpret_cast<const float4*>(row + m));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              float e = qa.x - xb[u].x;
+              float acc = fmaf(e, e, part[u0 + u]);
+              e = qa.y - xb[u].y;
               acc = fmaf(e, e, acc);
-              e = qa.z - xa.z;
+              e = qa.z - xb[u].z;
               acc = fmaf(e, e, acc);
-              e = qa.w - xa.w;
-              part[u] = fmaf(e, e, acc);
+              e = qa.w - xb[u].w;
+              part[u0 + u] = fmaf(e, e, acc);
             }
           }
         }
