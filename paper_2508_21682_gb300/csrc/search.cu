@@ -334,16 +334,16 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
           // used (an empty slot reads the query's own row; its result is
           // discarded)
 #pragma unroll
-          for (int u0 = 0; u0 < 32; u0 += 8) {
-            float4 xb[8];
+          for (int u0 = 0; u0 < 32; u0 += 16) {
+            float4 xb[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
               const uint32_t p = cpid[u0 + u];
               const float* row = p != 0xffffffffu ? a.x + (size_t)p * a.d : qv;
               xb[u] = __ldg(reinterpret_cast<const float4*>(row + m));
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
               float e = qa.x - xb[u].x;
               float acc = fmaf(e, e, part[u0 + u]);
               e = qa.y - xb[u].y;
