@@ -524,13 +524,24 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   cudaEvent_t a2 = tm.mark();
   tm.span(4, a0, a1);
   tm.span(7, a1, a2);
-  // first k of kp columns into the caller's buffers (device or host)
-  if (rc == HF_OK)
-    rc = map_cuda(cudaMemcpy2DAsync(out_idx, (size_t)k * 4, li, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
-                                    cudaMemcpyDefault, s));
-  if (rc == HF_OK)
-    rc = map_cuda(cudaMemcpy2DAsync(out_dist, (size_t)k * 4, ldd, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
-                                    cudaMemcpyDefault, s));
+  // First k of kp columns into the caller's buffers. A host buffer gets the
+  // columns packed on the device first and one contiguous copy (a strided
+  // copy of n rows of 4k bytes straight to the host moves at a fraction of
+  // the link's rate).
+  auto deliver = [&](void* out, const void* lists) -> int {
+    const size_t row = (size_t)k * 4, bytes = row * (size_t)n;
+    if (classify(out) == 1)
+      return map_cuda(cudaMemcpy2DAsync(out, row, lists, (size_t)kp * 4, row, (size_t)n, cudaMemcpyDefault, s));
+    void* packed = nullptr;
+    int r = map_cuda(dalloc_bytes(&packed, bytes, s));
+    if (r == HF_OK)
+      r = map_cuda(cudaMemcpy2DAsync(packed, row, lists, (size_t)kp * 4, row, (size_t)n, cudaMemcpyDefault, s));
+    if (r == HF_OK) r = map_cuda(cudaMemcpyAsync(out, packed, bytes, cudaMemcpyDefault, s));
+    dfree(packed, s);
+    return r;
+  };
+  if (rc == HF_OK) rc = deliver(out_idx, li);
+  if (rc == HF_OK) rc = deliver(out_dist, ldd);
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
   if (rc == HF_OK) tm.collect({4, 7});
