@@ -19,7 +19,6 @@
 // distance in float32 with exact coordinate differences from the float32
 // points, so the expansion's cancellation and the BF16 rounding never reach
 // the result; the list is re-sorted and the first k columns are the answer.
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -30,9 +29,7 @@
 namespace {
 
 constexpr int GB = 128;        // owned positions per block = MMA M
-constexpr int GT = 128;        // threads per block (4 warps, one per TMEM lane quarter)
 constexpr int KC = 64;         // BF16 elements per 128-byte K chunk
-constexpr uint32_t TMEM_COLS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -121,10 +118,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return desc;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // 16-byte asynchronous copy global -> shared (zero fill when !valid).
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   const int sz = valid ? 16 : 0;
@@ -203,24 +196,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// TMA gather of 4 rows (row coordinates r0..r3, columns [c, c + 64)) of the
-// BF16 point matrix into 4 consecutive 128-byte shared-memory lines, with the
-// tensor map's 128-byte swizzle; completion is counted in bytes on *bar.
-__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, int c, int r0, int r1, int r2, int r3,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5, %6}], [%7];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
-      : "memory");
-}
-
 struct PersistSmem {
   uint64_t full[STAGES], empty[STAGES];
   uint64_t tfull[2], tempty[2];
@@ -258,7 +233,7 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t l
 }
 
 template <int KP>
-__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
   extern __shared__ unsigned char smraw[];
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   const int N = a.N, nk = a.dp / KC;
@@ -617,7 +592,7 @@ size_t gram_smem(int N, int dp) {
 }
 
 template <int KP>
-int launch_gram_kp(const GramArgs& a, const CUtensorMap& map, size_t smem, cudaStream_t s) {
+int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
   if (cudaFuncSetAttribute((const void*)gram_window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
@@ -626,36 +601,9 @@ int launch_gram_kp(const GramArgs& a, const CUtensorMap& map, size_t smem, cudaS
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a, map);
+  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a);
   hf_after_launch("gram_window_kernel", s);
   return HF_OK;
-}
-
-// Tensor map of the BF16 point matrix [n][dp]: boxes of 64 elements x 1 row
-// (one 128-byte line per gathered row), 128-byte swizzle, zero fill outside.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-int make_row_map(CUtensorMap* map, const void* xb, int64_t n, int dp) {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !p)
-      return HF_ECUDA;
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  const cuuint64_t gdim[2] = {(cuuint64_t)dp, (cuuint64_t)n};
-  const cuuint64_t gstride[1] = {(cuuint64_t)dp * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)KC, 1};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(xb), gdim, gstride, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? HF_OK : HF_ECUDA;
 }
 
 }  // namespace
@@ -698,13 +646,10 @@ int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const
   // for more than half of the SM's shared memory
   size_t smem = gram_smem(a.N, a.dp);
   if (smem < 120 * 1024) smem = 120 * 1024;
-  alignas(64) CUtensorMap map;
-  const int rc = make_row_map(&map, xb, n, a.dp);
-  if (rc != HF_OK) return rc;
   switch (kp) {
-    case 16: return launch_gram_kp<16>(a, map, smem, s);
-    case 32: return launch_gram_kp<32>(a, map, smem, s);
-    case 64: return launch_gram_kp<64>(a, map, smem, s);
+    case 16: return launch_gram_kp<16>(a, smem, s);
+    case 32: return launch_gram_kp<32>(a, smem, s);
+    case 64: return launch_gram_kp<64>(a, smem, s);
     default: return HF_EINVAL;
   }
 }
