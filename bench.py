@@ -143,6 +143,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(v, dist, dev):
+    """The slowest rank's figure (every rank gets it); v itself with one rank.
+    The data path has no collective: ranks are independent replicas."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, n, ms_step):
+    """Whole-job points/s: every rank processes its own n points per step."""
+    return ws * n / (ms_step * 1e-3)
+
+
 def make_inputs(a, rank):
     import synthdata as S
     x = S.gaussian_mixture(a.n, a.d, n_components=a.components, seed=S.SEED_DATA + 1000 * rank)
@@ -235,11 +251,7 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize()
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    ms_step = sum(ms) / len(ms)
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(sum(ms) / len(ms), dist, dev)
 
     ph = {kk: statistics.mean(p[kk] for p in phases) for kk in phases[0]}
     launch_ms = ph["window_merge"] / T  # per launch (list init included, < 1%)
@@ -301,11 +313,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         if i:  # first one is a warm-up
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_step = statistics.mean(e2e_ms) if e2e_ms else float("nan")
-    if dist:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms) if e2e_ms else float("nan"), dist, dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -316,7 +324,7 @@ def run_ours(a):
         hs_ms = ph["keys"] + ph["sort"] + ph["tie_fixup"]
         line = {
             "metric": METRIC,
-            "value": ws * n / (ms_step * 1e-3),
+            "value": job_value(ws, n, ms_step),
             "unit": "points/s",
             "n_gpus": ws,
             "steps": a.steps,
@@ -338,7 +346,7 @@ def run_ours(a):
             "phase_ms": ph,
             "roofline": roof,
             "plain_f32": plain,
-            "e2e": {"value": ws * n / (e2e_step * 1e-3), "unit": "points/s",
+            "e2e": {"value": job_value(ws, n, e2e_step), "unit": "points/s",
                     "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
                     "ms_per_step": e2e_step},
