@@ -330,7 +330,7 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   // Trees are keyed and sorted in batches of TB (all of them when the
   // batch's scratch fits in half of the free device memory, 16 GiB at most).
   {
-    const int64_t ntiles = (n + 4095) / 4096;
+    const int64_t ntiles = (n + 2047) / 2048;  // sort tiles (status words per tile)
     const double per_tree = (double)n * (8.0 * f->K2 + 24.0) + (double)(ntiles + 1) * 256 * 4 * 8 * K;
     size_t fr = 0, tot = 0;
     double budget = 16.0 * (1ull << 30);

@@ -30,8 +30,8 @@
 namespace {
 
 constexpr int NT = 256;
-constexpr int IPT = 16;
-constexpr int TILE = NT * IPT;  // 4096 keys per tile
+constexpr int IPT = 8;
+constexpr int TILE = NT * IPT;  // 2048 keys per tile
 constexpr int WARPS = NT / 32;
 constexpr uint32_t FLAG_AGG = 1u << 30;
 constexpr uint32_t FLAG_PRE = 2u << 30;
@@ -135,7 +135,7 @@ struct PassArgs {
 // GATHER: the key of the element at position e is gather_src[vals_in[e]]
 // (the next prefix word, fetched in the current order).
 template <bool GATHER>
-__global__ void __launch_bounds__(NT, 3) onesweep_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(NT, 5) onesweep_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   PassSmem& S = *reinterpret_cast<PassSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
