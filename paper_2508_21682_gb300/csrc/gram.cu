@@ -503,7 +503,7 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[NV], int lane) {
 // distance in lane j. The KP entries are then re-sorted by (distance, index);
 // empty slots stay (+inf, 0xffffffff).
 template <int KP>
-__global__ void __launch_bounds__(256) rerank_kernel(const float* __restrict__ x, int64_t n, int d,
+__global__ void __launch_bounds__(256, 6) rerank_kernel(const float* __restrict__ x, int64_t n, int d,
                                                      const uint32_t* __restrict__ order, int vec4,
                                                      uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   constexpr int PER = (KP + 31) / 32;
