@@ -592,7 +592,7 @@ int sort_batch(hf_forest* f, int t0, int tb, cudaStream_t s) {
   cudaMemsetAsync(status, 0, per_pass * passes * sizeof(uint32_t), s);
   const size_t hsm = (size_t)hist_ts * sizeof(uint32_t);
   set_attr((const void*)digit_hist_kernel, hsm);
-  digit_hist_kernel<<<dim3(hf_blocks(n, 512, 152 * 2 / tb + 1), (unsigned)tb), 512, hsm, s>>>(f->pk, pk_ts, n, K,
+  digit_hist_kernel<<<dim3(hf_blocks(n, 512, 152 * 8 / tb + 1), (unsigned)tb), 512, hsm, s>>>(f->pk, pk_ts, n, K,
                                                                                             f->sort.hist);
   hf_after_launch("digit_hist_kernel", s);
   hist_scan_kernel<<<(unsigned)(tb * K * 8), 256, 0, s>>>(f->sort.hist);
