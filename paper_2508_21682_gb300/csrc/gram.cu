@@ -440,11 +440,11 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
         for (int jj = 0; jj < 32; ++jj) {
           const float2 e = snid[c0 + jj];
           const float d2 = np_ + e.x - 2.0f * __uint_as_float(v[jj]);
-          if (((wm >> jj) & 1u) && d2 <= td) {
-            mybd[m * 256] = d2;
-            mybi[m * 256] = __float_as_uint(e.y);
-            ++m;
-          }
+          // branch-free: always write slot m, keep it only on a hit (m <= jj,
+          // so 32 slots suffice)
+          mybd[m * 256] = d2;
+          mybi[m * 256] = __float_as_uint(e.y);
+          m += (((wm >> jj) & 1u) && d2 <= td) ? 1 : 0;
         }
 #pragma unroll 1
         for (int u = 0; u < m; ++u) L.offer(mybd[u * 256], mybi[u * 256]);
