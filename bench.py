@@ -48,7 +48,7 @@ METRIC = "kNN-graph points/s at recall@k>=0.8; Hilbert-sort Mkeys/s; % HBM/TC ro
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
 WINDOW_TRAFFIC = {"bytes_per_point": 1915, "source_sha": "c47a6c4277b03192", "file": "window.cu"}
-GRAM_TRAFFIC = {"bytes_per_point": 1134, "source_sha": "a0924b5e507153e2", "file": "gram.cu"}
+GRAM_TRAFFIC = {"bytes_per_point": 1134, "source_sha": "1ba5dabd3b9deee8", "file": "gram.cu"}
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
