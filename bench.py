@@ -43,6 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "kNN-graph points/s at recall@k>=0.8; Hilbert-sort Mkeys/s; % HBM/TC roofline"
+MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 
 # DRAM traffic of the dominant kernels from one ncu capture of a 1M-point
 # launch (bytes per point, scaled by n here) and the source file it was taken
@@ -72,10 +73,14 @@ def args():
     p.add_argument("--recall-sample", type=int, default=2000)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=60000)
-    p.add_argument("--mode", default="tensor", choices=["plain", "tensor"])
+    p.add_argument("--cpu-sample", type=int, default=4000, help="points per oracle process")
+    p.add_argument("--mode", default="tensor", choices=["plain", "tensor", "fp8"])
+    p.add_argument("--search-w", type=int, default=32, help="window of the query search (positions [p-w, p+w))")
     p.add_argument("--plain-steps", type=int, default=2, help="plain-mode steps timed beside tensor mode")
     p.add_argument("--tensor-slack", type=int, default=-1)
+    p.add_argument("--recall-sweep", default="",
+                   help="comma-separated T list x w list, e.g. '8,16,32,64,128,256:16,32,64,128,256': "
+                        "print the plain method's recall@k over that (T, w) grid and exit")
     return p.parse_args()
 
 
@@ -88,7 +93,7 @@ def dist_env():
 
 def workload_name(a):
     return (f"kNN graph + search: n={a.n} d={a.d} mixture({a.components}) T={a.T} b={a.bits} "
-            f"w={a.w} k={a.k}; {a.nq} queries")
+            f"w={a.w} k={a.k}; {a.nq} queries (w={a.search_w})")
 
 
 class ClockSampler:
@@ -222,11 +227,11 @@ def run_ours(a):
 
     def step(tim=None):
         G = hf.build(xd, T=T, bits=a.bits, seed=3)
-        if a.mode == "tensor":
-            G.set_option("mode", 1)
+        if a.mode != "plain":
+            G.set_option("mode", MODES[a.mode])
             G.set_option("tensor_slack", a.tensor_slack)
         G.knn_graph(k, w, gi, gd)
-        G.search(qd, k, w, si, sd)
+        G.search(qd, k, a.search_w, si, sd)
         if tim is not None:
             tim.append(G.timings())
         G.close()
@@ -255,14 +260,14 @@ def run_ours(a):
 
     ph = {kk: statistics.mean(p[kk] for p in phases) for kk in phases[0]}
     launch_ms = ph["window_merge"] / T  # per launch (list init included, < 1%)
-    if a.mode == "tensor":
+    if a.mode != "plain":
         roof = gram_roofline(a, launch_ms)
     else:
         roof = window_roofline(a, launch_ms)
 
     # plain float32 mode beside it (outside the timed region)
     plain = None
-    if a.mode == "tensor" and a.plain_steps > 0:
+    if a.mode != "plain" and a.plain_steps > 0:
         saved = a.mode
         a.mode = "plain"
         step()
@@ -304,11 +309,11 @@ def run_ours(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G = hf.build(xh, T=T, bits=a.bits, seed=3)
-        if a.mode == "tensor":
-            G.set_option("mode", 1)
+        if a.mode != "plain":
+            G.set_option("mode", MODES[a.mode])
             G.set_option("tensor_slack", a.tensor_slack)
         G.knn_graph(k, w, gih, gdh)
-        G.search(qh, k, w, sih, sdh)
+        G.search(qh, k, a.search_w, sih, sdh)
         G.close()
         torch.cuda.synchronize()
         if i:  # first one is a warm-up
@@ -322,6 +327,8 @@ def run_ours(a):
     if rank == 0:
         clocks = clk.summary()
         hs_ms = ph["keys"] + ph["sort"] + ph["tie_fixup"]
+        if int(round(ph.get("graph_form", 0.0))) != MODES[a.mode]:
+            raise SystemExit(f"asked for the {a.mode} form, the library ran form {ph.get('graph_form')}")
         line = {
             "metric": METRIC,
             "value": job_value(ws, n, ms_step),
@@ -333,13 +340,16 @@ def run_ours(a):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "bf16+f32" if a.mode == "tensor" else "f32",
+            "dtype": {"plain": "f32", "tensor": "bf16+f32", "fp8": "e4m3+f32"}[a.mode],
             "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
             "config": {"workload": workload_name(a), "n": n, "d": d, "T": T, "bits": a.bits, "w": w, "k": k,
-                       "queries": a.nq, "mode": "plain f32" if a.mode == "plain" else "bf16 tcgen05 Gram + f32 re-rank",
+                       "queries": a.nq, "mode": {"plain": "plain f32", "tensor": "bf16 tcgen05 Gram + f32 re-rank",
+                                              "fp8": "e4m3 tcgen05 Gram (scale per vector) + f32 re-rank"}[a.mode],
                        "l2": "inputs larger than L2 (points 4.6 GB per step)",
                        "parallelism": f"replicas x{ws}"},
             "recall_at_k": rec,
+            "at_metric_recall": bool(rec >= 0.8),
+            "keys_sort_hbm": keys_sort_hbm(a, ph),
             "recall_sample": int(len(rows)),
             "search_recall_at_k": rec_q,
             "hilbert_sort_mkeys_s": n * T / (hs_ms * 1e-3) / 1e6,
@@ -372,6 +382,29 @@ def measured_peaks():
             return json.load(fh), "of measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def keys_sort_hbm(a, ph):
+    """Achieved HBM bandwidth of key generation and of the radix sort, from
+    the library's phase timings (CUDA events on the launching stream).
+
+    Algorithmic bytes per point and tree: keys read the permuted top bits of
+    the point (d / 8 bytes of the bit-sliced top plane when the K-word prefix
+    lies in the top bit level, d * L / 8 bytes of planes otherwise) and write
+    K 64-bit words; the sort makes 8 K passes of 8-bit digits, each reading
+    and writing one 64-bit key word and one 32-bit index per point
+    (24 bytes)."""
+    K = min(2, -(-a.d * a.bits // 64))
+    L = min(a.bits, -(-64 * K // a.d))
+    kb = a.n * a.T * (a.d * L / 8 + 8 * K)
+    sb = a.n * a.T * 8 * K * 24
+    peaks, src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    out = {"peak": peak, "unit": "GB/s", "peak_note": f"hbm_gbs {src} (MEASURED_PEAKS.json)"}
+    for name, b, ms in (("keys", kb, ph["keys"]), ("sort", sb, ph["sort"])):
+        ach = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[name] = {"bytes": b, "ms": ms, "achieved": ach, "frac": ach / peak if ach else None}
+    return out
 
 
 def gram_roofline(a, launch_ms):
@@ -415,37 +448,124 @@ def oracle_sample(a, n_s, T_s, seed_offset=0):
     t0 = time.perf_counter()
     F = O.Forest(x, T=T_s, bits=a.bits, seed=3)
     O.knn_graph(F, a.k, a.w)
-    O.search(F, q, a.k, a.w)
+    O.search(F, q, a.k, a.search_w)
     return time.perf_counter() - t0
 
 
-def cpu_baseline(a):
+def _oracle_worker(args):
+    """One single-threaded oracle run (a spawned process of the pool)."""
+    a, n_s, T_s, seed_offset = args
     try:
         from threadpoolctl import threadpool_limits
-        lim = threadpool_limits(1)
+        threadpool_limits(1)
     except Exception:
-        lim = None
-    n_s, T_s = min(a.cpu_sample, a.n), 2
-    sec = oracle_sample(a, n_s, T_s)
-    if lim is not None:
-        lim.unregister() if hasattr(lim, "unregister") else None
-    # points/s of the full job: the sample's per-point, per-tree cost times T trees
-    val = n_s / (sec * a.T / T_s)
-    return {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
-            "sample": f"numpy oracle, {n_s} points of the same mixture, {T_s} of {a.T} trees, w={a.w}, k={a.k}, "
-                      f"queries pro rata; {sec:.1f} s; scaled to {a.T} trees"}
+        pass
+    return oracle_sample(a, n_s, T_s, seed_offset=seed_offset)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_parallel(a, procs, n_s, T_s, rounds=1):
+    """The oracle as it stands, one single-threaded process per core: procs
+    independent samples (each its own seeded data) run at once; returns the
+    whole-job points/s (points of all samples per second of wall time,
+    scaled from T_s to the workload's T trees) and the wall seconds."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")  # no fork of a process that has touched the GPU
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_worker, [(a, 500, 1, 100 + i) for i in range(procs)])  # imports, warm caches
+        walls = []
+        for r in range(rounds):
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [(a, n_s, T_s, 1000 * r + i) for i in range(procs)])
+            walls.append(time.perf_counter() - t0)
+    wall = statistics.mean(walls)
+    return procs * n_s / (wall * a.T / T_s), wall
+
+
+def cpu_baseline(a):
+    """The oracle on all host cores and on 8 of them (the paper's budget)."""
+    n_s, T_s = min(a.cpu_sample, a.n), 1
+    cores = host_cores()
+    val, wall = oracle_parallel(a, cores, n_s, T_s)
+    p8 = min(8, cores)
+    val8, wall8 = oracle_parallel(a, p8, n_s, T_s) if p8 != cores else (val, wall)
+    return {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(), "value_8": val8, "cores_8": p8,
+            "sample": f"numpy oracle (float64), one single-threaded process per core, each on its own {n_s} points "
+                      f"of the same mixture with {T_s} of {a.T} trees, w={a.w}, k={a.k}, queries pro rata "
+                      f"(w={a.search_w}); {wall:.1f} s wall on {cores} cores, {wall8:.1f} s on {p8}; "
+                      f"scaled to {a.T} trees"}
+
+
+def recall_sweep(a):
+    """Recall@k of the plain method over a (T, w) grid from one forest.
+
+    Point e is in point i's window of tree t exactly when their positions
+    differ by at most w (and e != i), and the graph's top k of a candidate set
+    C holds every true neighbour that C holds (they are the k nearest of all
+    points), so recall@k = |E(i) & C(i)| / k with E the exact k nearest. The
+    smallest position gap over the first T trees therefore gives recall at
+    every (T, w) at once."""
+    import torch
+    import paper_2508_21682_gb300 as hf
+    import __graft_entry__ as g
+    g.build()
+    ts_s, ws_s = a.recall_sweep.split(":")
+    Ts = sorted(int(v) for v in ts_s.split(","))
+    Ws = sorted(int(v) for v in ws_s.split(","))
+    dev = torch.device("cuda", 0)
+    x, _ = make_inputs(a, 0)
+    xd = torch.from_numpy(x).to(dev)
+    n = a.n
+    rng = np.random.default_rng(4)
+    rows = np.sort(rng.choice(n, size=min(a.recall_sample, n), replace=False))
+    rows_t = torch.from_numpy(rows).to(dev)
+    ex = torch.from_numpy(exact_knn_gpu(xd, xd[rows_t], a.k, exclude=rows_t)).to(dev)
+    t0 = time.perf_counter()
+    G = hf.build(xd, T=Ts[-1], bits=a.bits, seed=3)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sig = torch.empty(n, dtype=torch.int32, device=dev)
+    inv = torch.empty(n, dtype=torch.int64, device=dev)
+    ar = torch.arange(n, device=dev)
+    gap = torch.full(ex.shape, n, dtype=torch.int64, device=dev)
+    table = {}
+    for t in range(Ts[-1]):
+        G.order(t, out=sig)
+        inv[sig.long()] = ar
+        gap = torch.minimum(gap, (inv[ex] - inv[rows_t][:, None]).abs())
+        if t + 1 in Ts:
+            table[str(t + 1)] = {str(w): float((gap <= w).double().mean()) for w in Ws}
+    G.close()
+    print(json.dumps({"recall_sweep": table, "k": a.k, "n": n, "d": a.d, "sample": int(len(rows)),
+                      "build_s_T%d" % Ts[-1]: build_s, "workload": workload_name(a)}), flush=True)
 
 
 def run_reference(a):
     rank, ws, lr = dist_env()
     if rank != 0:
         return
-    n_s, T_s = min(10000, a.n), 1
-    for _ in range(a.warmup):
-        oracle_sample(a, n_s // 4, T_s)
-    secs = [oracle_sample(a, n_s, T_s, seed_offset=i) for i in range(a.steps)]
-    sec = statistics.mean(secs)
-    val = n_s / (sec * a.T / T_s)
+    n_s, T_s = min(a.cpu_sample, a.n), 1
+    cores = host_cores()
+    val, sec = oracle_parallel(a, cores, n_s, T_s, rounds=a.steps)
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -462,8 +582,9 @@ def run_reference(a):
         "data": "synthetic (seeded Gaussian mixture standing in for GOOAQ)",
         "config": {"workload": workload_name(a), "n": a.n, "d": a.d, "T": a.T, "bits": a.bits, "w": a.w,
                    "k": a.k, "queries": a.nq},
-        "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
-                         "sample": f"numpy oracle per step: {n_s} points, {T_s} of {a.T} trees, queries pro rata; "
+        "cpu_baseline": {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"numpy oracle (float64) per step: one single-threaded process per core, each on "
+                                   f"its own {n_s} points with {T_s} of {a.T} trees, queries pro rata; "
                                    f"scaled to {a.T} trees"},
         "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -474,5 +595,7 @@ if __name__ == "__main__":
     A = args()
     if A.impl == "reference":
         run_reference(A)
+    elif A.recall_sweep:
+        recall_sweep(A)
     else:
         run_ours(A)

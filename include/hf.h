@@ -75,6 +75,8 @@ enum {
 #define HF_MAX_BITS 8
 #define HF_MAX_K 64
 #define HF_MAX_N (((int64_t)1 << 30) - 1)
+/* Widest window of the plain float32 graph form (hf_set_option mode=0). */
+#define HF_PLAIN_MAX_W 704
 
 /*
  * hf_build -- preprocessing and the per-tree orders.
@@ -191,17 +193,23 @@ const char* hf_status_string(int status);
 
 /*
  * hf_set_option -- per-forest run-time options for later calls:
- *   mode=0  plain float32 window distances (default);
- *   mode=1  tensor-core window distances: BF16 Gram tiles (tcgen05, FP32
- *           accumulation) rank the candidates, each point keeps its best
- *           k + 1 (rounded up to 16, 32 or 64; see tensor_slack) by that
- *           estimate, and those are re-ranked by
- *           float32 exact-difference distance, so returned distances are exact
- *           float32 values; falls back to mode 0 for w > 64 or when one Gram
- *           tile (N = 128 + 2 ceil8(w) rows x ceil64(d) BF16) exceeds 220 KB of
- *           shared memory;
- *   tensor_slack=S  in mode 1, keep k + S candidates per point for the
- *           re-rank (rounded up to 16, 32 or 64; default S = 1);
+ *   mode=0  plain float32 window distances (default); w <= HF_PLAIN_MAX_W
+ *           (HF_ENOTIMPL beyond);
+ *   mode=1  tensor-core window distances: BF16 Gram bands (tcgen05, FP32
+ *           accumulation) estimate every candidate's distance, each point
+ *           keeps its best k + slack (rounded up to 16 or 32; see
+ *           tensor_slack) by that estimate, and those are re-ranked by
+ *           float32 exact-difference distance, so returned distances are
+ *           exact float32 values; any w >= 1;
+ *   mode=2  as mode 1 with FP8 e4m3 operands and one scale per vector
+ *           (s = max|x| / 448; tcgen05 kind::f8f6f4, FP32 accumulation);
+ *   modes 1 and 2 fall back to mode 0 when the Gram kernel's shared-memory
+ *   layout does not fit: for w > 64 a tile's 128 own rows stay resident next
+ *   to two or more stages of 256 rows, which holds up to d = 512 in mode 1
+ *   and d = 896 in mode 2 (hf_get_timings slot 8 reports the form that
+ *   ran); they return HF_ENOTIMPL when k + slack > 32;
+ *   tensor_slack=S  in modes 1 and 2, keep k + S candidates per point for
+ *           the re-rank (rounded up to 16 or 32; default S = 1);
  *   timing=1  record per-phase CUDA-event timings (default 1).
  * Unknown keys or values give HF_EINVAL.
  */
@@ -212,7 +220,10 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
  * [0] quantize, [1] keys, [2] sort (with the small-run fix-up), [3] big-run
  * fix-up, [4] window distances + merge (all trees; the Gram kernels in mode
  * 1), [5] search, [6] number of kernel launches of the last build (as a
- * float), [7] re-rank (mode 1). Writes min(cap, 8).
+ * float), [7] re-rank (modes 1, 2), [8] the form the last hf_knn_graph ran
+ * (0 = plain float32 window kernel, 1 = BF16 tensor-core Gram bands, 2 = FP8
+ * e4m3 Gram bands), so a caller that asked for a tensor form can see whether
+ * it fell back, [9..11] reserved (0). Writes min(cap, 12).
  */
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
 

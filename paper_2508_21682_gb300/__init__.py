@@ -233,9 +233,10 @@ class Forest:
         _check(lib().hf_set_option(self._h, key.encode(), value), "hf_set_option")
 
     def timings(self):
-        t = np.zeros(8, np.float32)
-        lib().hf_get_timings(self._h, t.ctypes.data, 8)
-        names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches", "rerank"]
+        t = np.zeros(12, np.float32)
+        lib().hf_get_timings(self._h, t.ctypes.data, 12)
+        names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches", "rerank",
+                 "graph_form"]
         return dict(zip(names, t.tolist()))
 
     # ---- inspection --------------------------------------------------------
@@ -249,9 +250,14 @@ class Forest:
         _check(lib().hf_debug_keys(self._h, tree, out.ctypes.data, None), "hf_debug_keys")
         return out
 
-    def order(self, tree: int):
-        out = np.empty(self.n, np.uint32)
-        _check(lib().hf_debug_order(self._h, tree, out.ctypes.data, None), "hf_debug_order")
+    def order(self, tree: int, out=None):
+        """sigma of tree `tree` (position -> point), uint32[n] on the host, or
+        written into `out` (a contiguous 4-byte tensor or array of n
+        elements, e.g. a CUDA int32 tensor) and returned."""
+        if out is None:
+            out = np.empty(self.n, np.uint32)
+        op, _o = _ptr(out)
+        _check(lib().hf_debug_order(self._h, tree, op, _stream(out)), "hf_debug_order")
         return out
 
     def locate(self, tree: int, queries):

@@ -68,12 +68,22 @@ cudaMemPool_t device_pool() {
   return g_pools[dev];
 }
 
-cudaError_t dalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
+}  // namespace
+
+cudaError_t hf_dalloc_bytes(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   cudaMemPool_t pool = device_pool();
   if (!pool) return cudaErrorMemoryAllocation;
   return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
 }
+
+void hf_dfree_bytes(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+namespace {
+
+cudaError_t dalloc_bytes(void** p, size_t bytes, cudaStream_t s) { return hf_dalloc_bytes(p, bytes, s); }
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
@@ -97,8 +107,10 @@ int map_cuda(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? HF_ENOMEM : HF_ECUDA;
 }
 
+}  // namespace
+
 // Synchronises, reads and clears the error word, maps to a status.
-int finish(hf_forest* f, cudaStream_t s) {
+int hf_finish(hf_forest* f, cudaStream_t s) {
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return map_cuda(e);
   e = cudaGetLastError();
@@ -110,6 +122,10 @@ int finish(hf_forest* f, cudaStream_t s) {
   if (word & HF_ERRBIT_TIMEOUT) return HF_ETIMEOUT;
   return HF_OK;
 }
+
+namespace {
+
+int finish(hf_forest* f, cudaStream_t s) { return hf_finish(f, s); }
 
 void free_build_scratch(hf_forest* f, cudaStream_t s) {
   dfree(f->pk, s);
@@ -139,7 +155,7 @@ void destroy(hf_forest* f, cudaStream_t s) {
   dfree(f->sigma, s);
   dfree(f->err, s);
   dfree(f->xb, s);
-  dfree(f->xnrm, s);
+  dfree(f->xmeta, s);
   delete f;
 }
 
@@ -184,7 +200,7 @@ struct Timer {
   hf_forest* f;
   cudaStream_t s;
   std::vector<cudaEvent_t> events;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[8];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[HF_NTIMINGS];
   explicit Timer(hf_forest* ff, cudaStream_t ss) : f(ff), s(ss) {}
   cudaEvent_t mark() {
     cudaEvent_t e = nullptr;
@@ -228,7 +244,8 @@ void hf_after_launch(const char* what, cudaStream_t s) {
     return v && *v && *v != '0';
   }();
   if (!on) return;
-  cudaError_t e = cudaGetLastError();
+  // peek: the error stays set for the entry point's final check
+  cudaError_t e = cudaPeekAtLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   fprintf(stderr, "[hf] %s: %s\n", what, cudaGetErrorString(e));
   fflush(stderr);
@@ -456,7 +473,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
   if (!f || !key) return HF_EINVAL;
   std::string k(key);
   if (k == "mode") {
-    if (value != 0 && value != 1) return HF_EINVAL;
+    if (value < 0 || value > 2) return HF_EINVAL;
     f->mode = (int)value;
   } else if (k == "tensor_slack") {
     if (value < -1 || value > 64) return HF_EINVAL;
@@ -471,7 +488,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
 
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap) {
   if (!f || !out_ms || cap < 0) return HF_EINVAL;
-  for (int i = 0; i < cap && i < 8; ++i) out_ms[i] = f->timings[i];
+  for (int i = 0; i < cap && i < HF_NTIMINGS; ++i) out_ms[i] = f->timings[i];
   return HF_OK;
 }
 
@@ -484,7 +501,6 @@ int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
 
 int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
   if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
-  if (w > 448) return HF_ENOTIMPL;  // widest window the band launches cover
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
@@ -492,17 +508,27 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= k + 1
   // (by default) by the BF16 expansion, then the re-rank orders them by exact
   // float32 distance. Either way the first k columns are the result.
-  const bool tensor = f->mode == 1 && gram_supported(f->d, w);
+  const int form = f->mode >= 1 && gram_supported(f->d, w, f->mode) ? f->mode : 0;
+  const bool tensor = form != 0;
+  if (!tensor && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;  // widest window the plain band launches cover
+  f->timings[8] = (float)form;  // the form that runs
   const int slack = f->tensor_slack < 0 ? 1 : f->tensor_slack;
   const int kp = window_list_pitch(tensor ? k + slack : k);
+  if (tensor && kp > 32) return HF_ENOTIMPL;  // tensor lists hold at most 32 entries
   uint32_t* li = nullptr;
   float* ldd = nullptr;
   cudaError_t e = dalloc(&li, (size_t)n * kp, s);
   if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp, s);
-  if (e == cudaSuccess && tensor && !f->xb) {
-    e = dalloc_bytes(&f->xb, (size_t)n * bf16_pitch(f->d) * 2, s);
-    if (e == cudaSuccess) e = dalloc(&f->xnrm, (size_t)n, s);
-    if (e == cudaSuccess) launch_prepare_bf16(f->x, n, f->d, f->xb, f->xnrm, s);
+  if (e == cudaSuccess && tensor && f->xform != form) {
+    dfree(f->xb, s);
+    dfree(f->xmeta, s);
+    f->xform = 0;
+    e = dalloc_bytes(&f->xb, (size_t)n * gram_row_bytes(f->d, form), s);
+    if (e == cudaSuccess) e = dalloc(&f->xmeta, (size_t)n, s);
+    if (e == cudaSuccess) {
+      launch_prepare_operands(f->x, n, f->d, form, f->xb, f->xmeta, s);
+      f->xform = form;
+    }
   }
   if (e != cudaSuccess) {
     dfree(li, s);
@@ -515,7 +541,8 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   int rc = HF_OK;
   for (int t = 0; t < f->T && rc == HF_OK; ++t) {
     if (tensor)
-      rc = launch_gram_window(f->xb, f->xnrm, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, f->err, s);
+      rc = launch_gram_window(f->xb, f->xmeta, form, n, f->d, f->sigma + (size_t)t * n, w, nullptr, nullptr, kp, li,
+                              ldd, f->err, s);
     else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }

@@ -1,25 +1,40 @@
 // Window distances on the tensor cores (tcgen05), then an exact re-rank.
 //
-// Paper, Algorithm 2: candidates are the neighbours around each position of
-// every sort; the final selection is by vector distance. The distance step is
-// the only dense contraction of the path: the squared distances between the
-// B = 128 points at positions [s, s+128) of one order and the N = 128 + 2 W8
-// points at positions [s - W8, s + 128 + W8) (W8 = w rounded up to 8) are
+// Paper, Algorithm 2: each sort contributes, for every point, the points
+// around its position as candidates; the final selection is by vector
+// distance. The distance step is the only dense contraction of the path. For
+// the 128 points at positions [s, s+128) of one order (a row tile) and the
+// points at positions [s - W8, s + 128 + W8) (W8 = w rounded up to 8; the
+// column range, Ncol = 128 + 2 W8 positions), the squared distances are
 //   d2(p, q) = |x_p|^2 + |x_q|^2 - 2 <x_p, x_q>,
-// and the inner products of a whole block are one 128 x N Gram tile. Here the
-// tile is computed by tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation
-// in tensor memory): the N gathered rows are staged once in shared memory in
-// the 128-byte-swizzled K-major layout; the 128 owned rows are rows W8 ..
-// W8+127 of that same tile, so both operands read one copy. The epilogue reads
-// each row's band (2w columns) out of tensor memory and merges approximate
-// distances (of the BF16-rounded vectors, expanded form) into the point's
-// top-KP list, KP >= 2k.
+// and the inner products are a 128 x Ncol Gram band. tcgen05.mma computes it
+// with FP32 accumulation in tensor memory from BF16 operands (kind::f16) or
+// from FP8 e4m3 operands with one scale per vector (kind::f8f6f4; x ~ s q, so
+// <x_p, x_q> ~ s_p s_q <q_p, q_q>).
+//
+// The column range is cut into units of at most 256 columns (one MMA each per
+// K step, N <= 256). When it fits one unit (W8 <= 64) the 128 owned rows are
+// rows W8 .. W8+127 of that unit's staged rows, so both operands read one
+// copy; otherwise the owned rows (the A operand) are staged once per tile in
+// a resident region, one slot per 128-byte K chunk, each slot refilled for the
+// next tile as soon as the tile's last MMA that reads it has completed. The
+// unit's rows (the B operand) stream through a ring of K-chunk stages. Rows
+// live in shared memory in the 128-byte-swizzled K-major layout.
+//
+// The epilogue reads each row's band (its 2w neighbours in the order) out of
+// tensor memory and merges the estimated distances into the point's top-KP
+// list (KP >= k + slack). Two halves of four warps share a tile: half h takes
+// the 32-column chunks of parity h, each half keeps its own list for the row,
+// and at the end of the tile half 1 hands its list to half 0 through shared
+// memory, which merges it and writes the point's list back.
 //
 // After the last tree, rerank_kernel recomputes every listed candidate's
 // distance in float32 with exact coordinate differences from the float32
-// points, so the expansion's cancellation and the BF16 rounding never reach
-// the result; the list is re-sorted and the first k columns are the answer.
+// points, so the expansion's cancellation and the operand rounding never
+// reach the result; the list is re-sorted and the first k columns are the
+// answer.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -28,8 +43,7 @@
 
 namespace {
 
-constexpr int GB = 128;        // owned positions per block = MMA M
-constexpr int KC = 64;         // BF16 elements per 128-byte K chunk
+constexpr int GB = 128;        // owned positions per tile = MMA M
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -83,6 +97,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same with e4m3 A and B (K = 32 per instruction, 32 bytes per row).
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrives on *bar once all MMAs issued so far by this thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -130,9 +153,9 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // BF16 copy of the points (row pitch dp, a multiple of 64, zero padded) and
-// the FP32 squared norms of the BF16-rounded rows.
+// per point (squared norm of the BF16-rounded row, scale 1).
 __global__ void prepare_bf16_kernel(const float* __restrict__ x, int64_t n, int d, int dp,
-                                    __nv_bfloat16* __restrict__ xb, float* __restrict__ nrm) {
+                                    __nv_bfloat16* __restrict__ xb, float2* __restrict__ meta) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -147,17 +170,54 @@ __global__ void prepare_bf16_kernel(const float* __restrict__ x, int64_t n, int 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) nrm[i] = s;
+    if (lane == 0) meta[i] = make_float2(s, 1.0f);
+  }
+}
+
+// FP8 e4m3 copy of the points with one scale per vector: s = max|x| / 448
+// (448 is the largest finite e4m3 value), q = e4m3(x / s) rounded to nearest
+// with saturation, row pitch dp (a multiple of 128, zero padded); per point
+// (float32 squared norm of x, s). A zero row gets s = 1 and q = 0.
+__global__ void prepare_fp8_kernel(const float* __restrict__ x, int64_t n, int d, int dp,
+                                   uint8_t* __restrict__ xq, float2* __restrict__ meta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float m = 0.f, s2 = 0.f;
+    for (int c = lane; c < d; c += 32) {
+      const float v = x[i * d + c];
+      m = fmaxf(m, fabsf(v));
+      s2 = fmaf(v, v, s2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const float sc = m > 0.f ? m / 448.0f : 1.0f;
+    for (int c = 2 * lane; c < dp; c += 64) {
+      const float v0 = c < d ? x[i * d + c] / sc : 0.f;
+      const float v1 = c + 1 < d ? x[i * d + c + 1] / sc : 0.f;
+      const __nv_fp8x2_storage_t p = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+      *reinterpret_cast<__nv_fp8x2_storage_t*>(xq + i * dp + c) = p;
+    }
+    if (lane == 0) meta[i] = make_float2(s2, sc);
   }
 }
 
 struct GramArgs {
-  const __nv_bfloat16* xb;
-  const float* nrm;
-  const uint32_t* sigma;
+  const uint8_t* xq;       // operand rows (BF16 or e4m3), pitch rowb bytes
+  const float2* meta;      // per point (squared norm, scale)
+  const uint32_t* sigma;   // order of this tree: position -> point
+  const int32_t* tile_w;   // per-tile window of this tree, or null (uniform w)
+  const uint16_t* pw;      // per-point window, or null (uniform w)
   int64_t n;
-  int dp, w, W8, N;
-  uint32_t idesc;
+  int rowb, nk;            // bytes per row (multiple of 128), K chunks
+  int w;                   // window when tile_w is null
+  int stages;              // B ring stages
+  uint32_t a_off, b_off, slot_off, x_off, bar_off;  // shared-memory layout
+  uint32_t b_stage_bytes;
   uint32_t* lidx;
   float* ldist;
   int* err;
@@ -165,44 +225,88 @@ struct GramArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised Gram kernel. One block per SM loops over tiles
-// (tile t = blockIdx.x + i * gridDim.x). Warps 0..3 (loaders) stage the
-// tile's row ids and norms in one of NSLOT slots (so they can run up to
-// NSLOT - 1 tiles ahead of the epilogue) and gather its rows into a ring of
-// STAGES K-chunk buffers with 16-byte asynchronous copies into the swizzled
-// layout; each thread keeps DEPTH chunks in flight and, once the oldest has
-// landed, issues a proxy fence and its arrival on that chunk's "full"
-// barrier. Warp 4 (MMA) issues the chunk's four K = 16 MMAs into one of two
-// tensor-memory accumulators and releases the chunk buffer through
-// tcgen05.commit. Warps 5..8 and 9..12 form two epilogue groups that take
-// alternate tiles (one accumulator each): each thread owns one row
-// (tensor-memory lane), screens its band and merges into the point's list,
-// then releases the accumulator and the staged slot.
-// Every wait on a barrier is bounded; when one gives up, the block raises the
-// error word, every role leaves its loop, and tensor memory is freed after a
-// bounded wait for MMAs in flight.
+// Persistent, warp-specialised band kernel. One block per SM loops over row
+// tiles t = blockIdx.x + i * gridDim.x and, within a tile, over its units
+// (unit j = columns [256 j, 256 j + Nj) of the tile's column range).
+//   warps 0..3  loaders: per K chunk of a unit, the unit's rows into the B
+//               ring with 16-byte cp.async copies into the swizzled layout; a
+//               stage is full once every loader's copies have landed
+//               (cp.async.mbarrier.arrive: no loader waits for its copies);
+//   warp 4      MMA issuer (one lane): per unit, all K chunks into one of two
+//               tensor-memory accumulators (256 columns each);
+//   warp 5      prep: per unit, the (norm, scale, id) of its columns (and, for
+//               the first unit, of the tile's own rows) into one of NSLOT
+//               slots; per tile with several units, the own rows into the
+//               resident A region;
+//   warps 6..13 epilogue: a warp owns tensor-memory lanes 32 (warp % 4) ..
+//               + 31 (tile rows) and, in half h = (warp - 6) / 4, the
+//               32-column chunks of parity h.
+// Every barrier wait is bounded (spin_limit ns of %globaltimer); when one
+// gives up, the block raises the error word, every role leaves, and tensor
+// memory is freed after a bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
-constexpr int STAGES = 4;
-constexpr int NSLOT = 4;           // staged (norm, id) rows: tiles the loaders may run ahead
-constexpr int DEPTH = 3;           // K chunks a loader keeps in flight (< STAGES)
-constexpr int PER = 16;            // 16-byte pieces per loader thread and chunk
-constexpr int LW = 4;              // loader warps (warps 0..3)
+constexpr int NSLOT = 4;           // staged (norm, scale, id) units: loaders run ahead
+constexpr int SLOT_COLS = 256;     // column entries per slot
+constexpr int SLOT_ENTS = SLOT_COLS + GB;  // + the tile's own rows
+constexpr int XE = 16;             // list entries handed over per exchange round
+constexpr int LW = 4;              // loader warps 0..3
 constexpr int MW = LW;             // MMA warp
-constexpr int EW0 = LW + 1;        // first epilogue warp (two groups of 4)
-constexpr int PT = (LW + 1 + 8) * 32;
+constexpr int PW = LW + 1;         // prep warp: slots and the resident A rows
+constexpr int EW0 = LW + 2;        // first epilogue warp
+constexpr int PT = (LW + 2 + 8) * 32;
 constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
+constexpr int MAX_STAGES = 4;
+constexpr int A_PER = GB * 8 / 32;          // A pieces per prep lane and chunk (32)
+constexpr int B_PER = 256 * 8 / (LW * 32);  // B pieces per loader thread and chunk (16)
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
+// One arrival on *bar once every cp.async this thread has issued so far has
+// landed (the barrier's expected count includes this thread).
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
-struct PersistSmem {
-  uint64_t full[STAGES], empty[STAGES];
+struct Bars {
+  uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+  uint64_t afull[32], aempty[32];    // per resident A chunk (K chunks <= 32)
   uint64_t tfull[2], tempty[2];
   uint64_t mfull[NSLOT], mempty[NSLOT];
+  uint64_t xfull[4], xempty[4];
   uint32_t tslot;
   int abort;
 };
+
+// One staged column (or own row): BF16 needs (norm, id), FP8 also the scale.
+struct EntB {
+  float nrm;
+  uint32_t id;
+};
+struct EntF {
+  float nrm, sc;
+  uint32_t id, pad;
+};
+template <bool F8>
+struct EntOf {
+  using T = EntB;
+};
+template <>
+struct EntOf<true> {
+  using T = EntF;
+};
+__device__ __forceinline__ void ent_set(EntB& e, float n, float, uint32_t id) {
+  e.nrm = n;
+  e.id = id;
+}
+__device__ __forceinline__ void ent_set(EntF& e, float n, float s, uint32_t id) {
+  e.nrm = n;
+  e.sc = s;
+  e.id = id;
+  e.pad = 0;
+}
+__device__ __forceinline__ float ent_sc(const EntB&) { return 1.0f; }
+__device__ __forceinline__ float ent_sc(const EntF& e) { return e.sc; }
 
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
@@ -232,35 +336,77 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t l
   return true;
 }
 
-template <int KP>
-__global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
+// The tile's window (0 = no row of the tile takes part), W8, column count
+// and unit count.
+struct TileGeom {
+  int w, W8, ncol, J;
+};
+__device__ __forceinline__ TileGeom tile_geom(const GramArgs& a, int64_t t) {
+  TileGeom g;
+  g.w = a.tile_w ? __ldg(a.tile_w + t) : a.w;
+  if (g.w <= 0) {
+    g.w = g.W8 = g.ncol = g.J = 0;
+    return g;
+  }
+  g.W8 = (g.w + 7) & ~7;
+  g.ncol = GB + 2 * g.W8;
+  g.J = (g.ncol + SLOT_COLS - 1) / SLOT_COLS;
+  return g;
+}
+
+
+// v[j] of a register array (j known only at run time): a 5-level select tree.
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], int j) {
+  uint32_t a16[16], a8[8], a4[4], a2[2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a16[i] = (j & 16) ? v[i + 16] : v[i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a8[i] = (j & 8) ? a16[i + 8] : a16[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a4[i] = (j & 4) ? a8[i + 4] : a8[i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a2[i] = (j & 2) ? a4[i + 2] : a4[i];
+  return (j & 1) ? a2[1] : a2[0];
+}
+
+template <int KP, bool F8>
+__global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
+  using Ent = typename EntOf<F8>::T;
   extern __shared__ unsigned char smraw[];
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
-  const int N = a.N, nk = a.dp / KC;
-  const size_t stage_bytes = (size_t)N * 128;
-  const int NP = N + 32;  // padded: an epilogue chunk may run past column N - 1
-  float2* mnid = reinterpret_cast<float2*>(base + STAGES * stage_bytes);  // [NSLOT][NP] (norm, id bits)
-  float* cbd = reinterpret_cast<float*>(mnid + NSLOT * NP);               // [32][256]
-  uint32_t* cbi = reinterpret_cast<uint32_t*>(cbd + 256 * 32);            // [32][256]
-  PersistSmem& S = *reinterpret_cast<PersistSmem*>(cbi + 256 * 32);
+  unsigned char* aregion = base + a.a_off;
+  unsigned char* bring = base + a.b_off;
+  Ent* slots = reinterpret_cast<Ent*>(base + a.slot_off);
+  float* xd = reinterpret_cast<float*>(base + a.x_off);            // [XE][128] distances
+  uint32_t* xi = reinterpret_cast<uint32_t*>(xd + XE * GB);        // [XE][128] indices
+  Bars& S = *reinterpret_cast<Bars*>(base + a.bar_off);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const uint64_t lim = a.spin_limit;
+  const int nk = a.nk, stages = a.stages;
 
   if (warp == MW) tmem_alloc(&S.tslot, TMEM_ALL);
   if (tid == 0) {
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < stages; ++i) {
       mbar_init(&S.full[i], LW * 32);
       mbar_init(&S.empty[i], 1);
     }
+    for (int i = 0; i < nk; ++i) {
+      mbar_init(&S.afull[i], 32);
+      mbar_init(&S.aempty[i], 1);
+    }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.tfull[i], 1);
-      mbar_init(&S.tempty[i], 4);
+      mbar_init(&S.tempty[i], 8);
     }
     for (int i = 0; i < NSLOT; ++i) {
-      mbar_init(&S.mfull[i], 1);
-      mbar_init(&S.mempty[i], 4);
+      mbar_init(&S.mfull[i], 32);
+      mbar_init(&S.mempty[i], 8);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&S.xfull[i], 32);
+      mbar_init(&S.xempty[i], 32);
     }
     S.abort = 0;
     fence_mbar_init();
@@ -272,190 +418,296 @@ __global__ void __launch_bounds__(PT, 1) gram_window_kernel(GramArgs a) {
   volatile int* abort = &S.abort;
 
   if (warp < LW) {
-    // ---------------- loaders: 128 threads
-    const int lt = tid;  // 0 .. 127
-    uint32_t it = 0;     // chunk counter across tiles
-    int pending = 0;     // chunks issued but not yet marked full
-    int tl = 0;
-    // Row ids (and then norms) of the next tile are loaded into registers
-    // while the current tile streams, so a tile starts without a dependent
-    // pair of global round trips. Thread lt stages rows lt + 128 j.
-    constexpr int RPT = 3;  // ceil((N + 32) / 128) for N <= 256
-    uint32_t npid[RPT];
-    float nnrm[RPT];
-    auto fetch_ids = [&](int64_t tt) {
-      const int64_t rr0 = tt * GB - a.W8;
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        const int r = lt + j * LW * 32;
-        const int64_t p = rr0 + r;
-        npid[j] = (tt < ntiles && r < N && p >= 0 && p < a.n) ? __ldg(a.sigma + p) : 0xffffffffu;
-      }
-    };
-    auto fetch_norms = [&]() {
-#pragma unroll
-      for (int j = 0; j < RPT; ++j)
-        nnrm[j] = npid[j] != 0xffffffffu ? __ldg(a.nrm + npid[j]) : __uint_as_float(0x7fc00000u);
-    };
-    fetch_ids(blockIdx.x);
-    fetch_norms();
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
-      const int slot = tl % NSLOT;
-      const uint32_t suse = (uint32_t)(tl / NSLOT);
-      if (!pwait(&S.mempty[slot], (suse & 1) ^ 1, lim, abort, a.err)) break;
-      float2* snid = mnid + slot * NP;
-      // rows outside the matrix get a NaN norm: their distances never pass a screen
-#pragma unroll
-      for (int j = 0; j < RPT; ++j) {
-        const int r = lt + j * LW * 32;
-        if (r < NP) snid[r] = make_float2(nnrm[j], __uint_as_float(npid[j]));
-      }
-      fetch_ids(t + gridDim.x);
-      asm volatile("bar.sync 1, %0;" ::"r"(LW * 32) : "memory");  // loaders only
-      if (lt == 0) mbar_arrive(&S.mfull[slot]);
-      // this thread's pieces: the same (row, 16-byte column) in every chunk,
-      // so sources and swizzled destinations are formed once per tile
-      const __nv_bfloat16* src[PER];
-      uint32_t dsto[PER];
-      uint32_t lmask = 0, smask = 0;  // pieces to load / to store
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int e = lt + q * LW * 32;
-        const int r = e >> 3, j = e & 7;
-        const uint32_t pid = e < N * 8 ? __float_as_uint(snid[r].y) : 0xffffffffu;
-        src[q] = a.xb + (pid != 0xffffffffu ? (size_t)pid * a.dp : 0) + j * 8;
-        dsto[q] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
-        if (e < N * 8) smask |= 1u << q;
-        if (pid != 0xffffffffu) lmask |= 1u << q;
-      }
-      bool ok = true;
-      for (int kc = 0; kc < nk; ++kc, ++it) {
-        const int st = it % STAGES;
-        if (!pwait(&S.empty[st], ((it / STAGES) & 1) ^ 1, lim, abort, a.err)) {
+    // ---------------- loaders: 128 threads. Each copies its pieces of a
+    // chunk and leaves; the stage's "full" barrier completes once every
+    // loader's copies have landed (cp.async.mbarrier.arrive), so a loader
+    // only ever waits for a stage to be released or for a slot's ids.
+    const int lt = tid;
+    uint32_t it = 0, u = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileGeom g = tile_geom(a, t);
+      for (int j = 0; j < g.J && ok; ++j, ++u) {
+        const int sl = u % NSLOT;
+        const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
+        if (!pwait(&S.mfull[sl], (u / NSLOT) & 1, lim, abort, a.err)) {
           ok = false;
           break;
         }
-        const uint32_t dst0 = smem_u32(base + st * stage_bytes);
+        const Ent* se = slots + sl * SLOT_ENTS;
+        // this thread's pieces: the same (row, 16-byte column) in every chunk
+        const uint8_t* bsrc[B_PER];
+        uint32_t bdst[B_PER];
+        uint32_t bstore = 0, bload = 0;
 #pragma unroll
-        for (int q = 0; q < PER; ++q)
-          if ((smask >> q) & 1u) cp_async16(dst0 + dsto[q], src[q] + kc * KC, (lmask >> q) & 1u);
-        cp_async_commit();
-        // keep DEPTH chunks in flight: once the oldest has landed, make its
-        // stores visible to the tensor core and mark its stage full
-        if (++pending == DEPTH) {
-          cp_async_wait<DEPTH - 1>();
-          fence_proxy_async_smem();
-          mbar_arrive(&S.full[(it - (DEPTH - 1)) % STAGES]);
-          --pending;
+        for (int q = 0; q < B_PER; ++q) {
+          const int e = lt + q * LW * 32;
+          const int r = e >> 3, pc = e & 7;
+          const uint32_t pid = r < nj ? se[r].id : 0xffffffffu;
+          bsrc[q] = a.xq + (pid != 0xffffffffu ? (size_t)pid * a.rowb : 0) + pc * 16;
+          bdst[q] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((pc ^ (r & 7)) << 4));
+          if (r < nj) bstore |= 1u << q;
+          if (pid != 0xffffffffu) bload |= 1u << q;
+        }
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int st = it % stages;
+          if (!pwait(&S.empty[st], ((it / stages) & 1) ^ 1, lim, abort, a.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t d0 = smem_u32(bring + (size_t)st * a.b_stage_bytes);
+#pragma unroll
+          for (int q = 0; q < B_PER; ++q)
+            if ((bstore >> q) & 1u) cp_async16(d0 + bdst[q], bsrc[q] + kc * 128, (bload >> q) & 1u);
+          cp_async_arrive(&S.full[st]);
         }
       }
-      fetch_norms();  // the next tile's ids have arrived by now
-      if (!ok) break;
-      if (nk < DEPTH) {
-        // a later tile's accumulator wait must not depend on this tile's
-        // chunks still being held back
-        cp_async_wait<0>();
-        fence_proxy_async_smem();
-        for (; pending > 0; --pending) mbar_arrive(&S.full[(it - pending) % STAGES]);
+    }
+    cp_async_commit();  // no copy of this thread may be in flight at exit
+    cp_async_wait<0>();
+  } else if (warp == PW) {
+    // ---------------- prep warp: per unit, the (norm, scale, id) of its
+    // columns and (first unit) of the tile's own rows into a slot, ahead of
+    // the loaders; per tile whose band needs several units, the own rows into
+    // the resident A region, chunk kc as soon as the previous tile's last MMA
+    // reading that chunk has completed
+    uint32_t u = 0, auses = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileGeom g = tile_geom(a, t);
+      const int64_t s = t * GB, c_lo = s - g.W8;
+      for (int j = 0; j < g.J && ok; ++j, ++u) {
+        const int sl = u % NSLOT;
+        const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
+        if (!pwait(&S.mempty[sl], ((u / NSLOT) & 1) ^ 1, lim, abort, a.err)) {
+          ok = false;
+          break;
+        }
+        Ent* se = slots + sl * SLOT_ENTS;
+        // rows outside the matrix get a NaN norm: they never pass a screen
+        uint32_t ids[SLOT_ENTS / 32];
+#pragma unroll
+        for (int m = 0; m < SLOT_ENTS / 32; ++m) {
+          const int e = lane + 32 * m;
+          int64_t pos;
+          bool valid;
+          if (e < SLOT_COLS) {
+            pos = c_lo + (int64_t)SLOT_COLS * j + e;
+            valid = e < nj && pos >= 0 && pos < a.n;
+          } else {
+            pos = s + (e - SLOT_COLS);
+            valid = j == 0 && pos < a.n;
+          }
+          ids[m] = valid ? __ldg(a.sigma + pos) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int m = 0; m < SLOT_ENTS / 32; ++m) {
+          const float2 mt =
+              ids[m] != 0xffffffffu ? __ldg(a.meta + ids[m]) : make_float2(__uint_as_float(0x7fc00000u), 0.f);
+          Ent en;
+          ent_set(en, mt.x, mt.y, ids[m]);
+          se[lane + 32 * m] = en;
+        }
+        mbar_arrive(&S.mfull[sl]);
+        if (g.J > 1 && j == 0) {
+          __syncwarp();  // the own rows' ids written by the other lanes
+          const uint32_t par = (auses & 1) ^ 1;
+          for (int kc = 0; kc < nk && ok; ++kc) {
+            if (!pwait(&S.aempty[kc], par, lim, abort, a.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t d0 = smem_u32(aregion + (size_t)kc * GB * 128);
+#pragma unroll 4
+            for (int q = 0; q < A_PER; ++q) {
+              const int e = lane + 32 * q;
+              const int r = e >> 3, pc = e & 7;
+              const uint32_t pid = se[SLOT_COLS + r].id;
+              const uint8_t* src = a.xq + (pid != 0xffffffffu ? (size_t)pid * a.rowb : 0) + kc * 128 + pc * 16;
+              cp_async16(d0 + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((pc ^ (r & 7)) << 4)), src,
+                         pid != 0xffffffffu);
+            }
+            cp_async_arrive(&S.afull[kc]);
+          }
+          ++auses;
+        }
       }
     }
-    // the last chunks (also after an abort: no copy may be in flight at exit)
+    cp_async_commit();
     cp_async_wait<0>();
-    fence_proxy_async_smem();
-    for (; pending > 0; --pending) mbar_arrive(&S.full[(it - pending) % STAGES]);
   } else if (warp == MW) {
     // ---------------- MMA issuer (one lane)
     if (lane == 0) {
-      uint32_t it = 0;
-      int tl = 0;
-      const uint32_t sb = smem_u32(base);
-      for (int64_t t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++tl) {
-        const int buf = tl & 1;
-        const uint32_t use = (uint32_t)(tl >> 1);
-        if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) break;
-        tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(buf * 256);
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int st = it % STAGES;
-          if (!pwait(&S.full[st], (it / STAGES) & 1, lim, abort, a.err)) break;
-          tc_fence_after();
-          const uint32_t chunk = sb + (uint32_t)(st * stage_bytes);
-#pragma unroll
-          for (int ks = 0; ks < KC / 16; ++ks) {
-            const uint64_t bdesc = smem_desc(chunk + ks * 32);
-            const uint64_t adesc = smem_desc(chunk + (a.W8 >> 3) * 1024 + ks * 32);
-            mma_bf16(acc, adesc, bdesc, a.idesc, (kc | ks) != 0);
+      uint32_t it = 0, u = 0, auses = 0;
+      const uint32_t bb = smem_u32(bring), ab = smem_u32(aregion);
+      // FP32 accumulator; BF16 A and B (kind::f16) or e4m3 A and B
+      // (kind::f8f6f4); both K-major; M >> 4 at bit 24, N >> 3 at bit 17
+      const uint32_t id0 = (1u << 4) | (F8 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(GB >> 4) << 24);
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok && !*abort; t += gridDim.x) {
+        const TileGeom g = tile_geom(a, t);
+        for (int j = 0; j < g.J; ++j, ++u) {
+          const int buf = u & 1;
+          const uint32_t use = u >> 1;
+          if (!pwait(&S.tempty[buf], (use & 1) ^ 1, lim, abort, a.err)) {
+            ok = false;
+            break;
           }
-          mma_commit(&S.empty[st]);
+          tc_fence_after();
+          const uint32_t acc = tmem + (uint32_t)(buf * 256);
+          const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
+          const uint32_t idesc = id0 | ((uint32_t)(nj >> 3) << 17);
+          for (int kc = 0; kc < nk; ++kc, ++it) {
+            const int st = it % stages;
+            if (!pwait(&S.full[st], (it / stages) & 1, lim, abort, a.err) ||
+                (g.J > 1 && !pwait(&S.afull[kc], auses & 1, lim, abort, a.err))) {
+              ok = false;
+              break;
+            }
+            // the stage was written by cp.async (generic proxy) and is read
+            // by the tensor core (async proxy)
+            fence_proxy_async_smem();
+            tc_fence_after();
+            const uint32_t chunk = bb + (uint32_t)(st * a.b_stage_bytes);
+            const uint32_t achunk = g.J == 1 ? chunk + (uint32_t)(g.W8 >> 3) * 1024u : ab + (uint32_t)kc * GB * 128u;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t bdesc = smem_desc(chunk + ks * 32);
+              const uint64_t adesc = smem_desc(achunk + ks * 32);
+              if (F8)
+                mma_f8(acc, adesc, bdesc, idesc, (kc | ks) != 0);
+              else
+                mma_bf16(acc, adesc, bdesc, idesc, (kc | ks) != 0);
+            }
+            mma_commit(&S.empty[st]);
+            if (g.J > 1 && j == g.J - 1) mma_commit(&S.aempty[kc]);
+          }
+          if (!ok) break;
+          mma_commit(&S.tfull[buf]);
         }
-        mma_commit(&S.tfull[buf]);
+        if (g.J > 1) ++auses;
       }
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: group 0 = warps 5..8 (accumulator 0, even
-    // tiles), group 1 = warps 9..12 (accumulator 1, odd tiles); within a
-    // group, warp w owns tensor-memory lanes 32 (w % 4) .. + 31
-    const int grp = (warp - EW0) >> 2;
-    const int quarter = warp & 3;
-    const int r = quarter * 32 + lane;  // tile row = TMEM lane
-    // staged candidates: entry u of thread `slot` at [u][slot] (conflict-free)
-    const int slot = grp * 128 + r;
-    float* mybd = cbd + slot;
-    uint32_t* mybi = cbi + slot;
-    const int buf = grp;
-    int tl = grp;
-    for (int64_t t = blockIdx.x + (int64_t)grp * gridDim.x; t < ntiles && !*abort;
-         t += 2 * (int64_t)gridDim.x, tl += 2) {
-      const uint32_t use = (uint32_t)(tl >> 1);
-      const int sl = tl % NSLOT;
-      if (!pwait(&S.mfull[sl], (tl / NSLOT) & 1, lim, abort, a.err)) break;
-      // the row's list is fetched while the tile's MMAs run
-      const float2* snid = mnid + sl * NP;
+    // ---------------- epilogue: warp EW0 + q + 4 h owns tensor-memory lanes
+    // 32 q .. 32 q + 31 (tile rows) and the 32-column chunks of parity h
+    const int h = (warp - EW0) >> 2;
+    const int q = warp & 3;       // a warp may access TMEM lanes 32 (warp % 4) .. + 31
+    const int r = q * 32 + lane;  // tile row = TMEM lane
+    uint32_t u = 0, xr = 0;
+    bool ok = true;
+    // waits and exits are warp-uniform: tcgen05.ld is .sync.aligned
+    auto wwait = [&](uint64_t* bar, uint32_t par) {
+      return __all_sync(0xffffffffu, pwait(bar, par, lim, abort, a.err));
+    };
+    for (int64_t t = blockIdx.x; t < ntiles && ok && !__any_sync(0xffffffffu, *abort); t += gridDim.x) {
+      const TileGeom g = tile_geom(a, t);
+      if (g.J == 0) continue;
       const int64_t p = t * GB + r;
       const bool rowok = p < a.n;
       ListK<KP> L;
-      const float2 own = snid[r + a.W8];
-      const uint32_t ip = __float_as_uint(own.y);
-      if (rowok) L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
-      if (!pwait(&S.tfull[buf], use & 1, lim, abort, a.err)) break;
-      tc_fence_after();
-      const float np_ = own.x;
-      // the row's band: columns [r + W8 - w, r + W8 + w] except r + W8 itself
-      const int wlo = r + a.W8 - a.w, whi = r + a.W8 + a.w, diag = r + a.W8;
-      const int cfirst = 32 * quarter;
-      const int clast = 32 * quarter + 31 + 2 * a.W8;
-      for (int c0 = cfirst; c0 <= clast && c0 < N; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (uint32_t)(buf * 256) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
-        const int lo = wlo - c0 > 0 ? wlo - c0 : 0;
-        const int hi = whi - c0 < 31 ? whi - c0 : 31;
-        uint32_t wm = 0;
-        if (rowok && lo <= hi) wm = (0xffffffffu >> (31 - hi + lo)) << lo;
-        if (diag >= c0 && diag < c0 + 32) wm &= ~(1u << (diag - c0));
-        // screen against the current last entry (ties pass; the offer decides)
-        const float td = L.d[KP - 1];
-        int m = 0;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const float2 e = snid[c0 + jj];
-          const float d2 = np_ + e.x - 2.0f * __uint_as_float(v[jj]);
-          // branch-free: always write slot m, keep it only on a hit (m <= jj,
-          // so 32 slots suffice)
-          mybd[m * 256] = d2;
-          mybi[m * 256] = __float_as_uint(e.y);
-          m += (((wm >> jj) & 1u) && d2 <= td) ? 1 : 0;
+      float ni = 0.f, c2 = 2.0f;
+      uint32_t ip = 0xffffffffu;
+      int wlo = 0, whi = -1;
+      for (int j = 0; j < g.J; ++j, ++u) {
+        const int sl = u % NSLOT, buf = u & 1;
+        const uint32_t use = u >> 1;
+        if (!wwait(&S.mfull[sl], (u / NSLOT) & 1)) {
+          ok = false;
+          break;
         }
+        const Ent* se = slots + sl * SLOT_ENTS;
+        if (j == 0) {
+          const Ent own = se[SLOT_COLS + r];
+          ip = own.id;
+          ni = own.nrm;
+          c2 = 2.0f * ent_sc(own);
+          int wr = g.w;
+          if (rowok && a.pw) wr = min(wr, (int)__ldg(a.pw + ip));
+          // the row's band: columns [r + W8 - wr, r + W8 + wr] except r + W8
+          wlo = r + g.W8 - wr;
+          whi = rowok ? r + g.W8 + wr : -1;
+          // both halves start from the point's list (fetched while the MMAs
+          // run), so both screen against its current last entry; half 0
+          // writes the merged list back
+          if (rowok)
+            L.load(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
+          else
+            L.clear();
+        }
+        if (!wwait(&S.tfull[buf], use & 1)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int u0 = SLOT_COLS * j;
+        const int wb_hi = 32 * q + 31 + 2 * g.W8;  // last band column of the warp
+        const int diag = r + g.W8;
+        // chunks [c0, c0 + 32) of the warp's band inside this unit, parity h
+        int c0 = max(32 * q, u0);
+        if (((c0 >> 5) & 1) != h) c0 += 32;
+        for (; c0 <= wb_hi && c0 < u0 + SLOT_COLS; c0 += 64) {
+          __syncwarp();  // reconverge after the divergent inserts
+          uint32_t v[32];
+          tmem_ld32(tmem + (uint32_t)(buf * 256) + ((uint32_t)(32 * q) << 16) + (uint32_t)(c0 - u0), v);
+          const int lo = wlo - c0 > 0 ? wlo - c0 : 0;
+          const int hi = whi - c0 < 31 ? whi - c0 : 31;
+          uint32_t wm = 0;
+          if (lo <= hi) wm = (0xffffffffu >> (31 - hi + lo)) << lo;
+          if (diag >= c0 && diag < c0 + 32) wm &= ~(1u << (diag - c0));
+          // screen against the current last entry (ties pass; the offer
+          // decides); the estimates stay in registers for the hits
+          const float td = L.d[KP - 1];
+          const Ent* ce = se + (c0 - u0);
+          uint32_t hm = 0;
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const Ent e = ce[jj];
+            const float dot = __uint_as_float(v[jj]);
+            const float d2 = F8 ? fmaf(-c2 * ent_sc(e), dot, ni + e.nrm) : fmaf(-2.0f, dot, ni + e.nrm);
+            v[jj] = __float_as_uint(d2);  // the estimate replaces the dot product
+            hm |= (d2 <= td ? 1u : 0u) << jj;
+          }
+          hm &= wm;
+          while (hm) {
+            const int jj = __ffs(hm) - 1;
+            hm &= hm - 1;
+            L.offer(__uint_as_float(pick32(v, jj)), ce[jj].id);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&S.tempty[buf]);
+          mbar_arrive(&S.mempty[sl]);
+        }
+      }
+      if (!ok) break;
+      // half 1 hands its list to half 0 in rounds of XE entries
+      for (int e0 = 0; e0 < KP && ok; e0 += XE, ++xr) {
+        if (h == 1) {
+          if (!wwait(&S.xempty[q], (xr & 1) ^ 1)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int e = 0; e < XE; ++e) {
+            xd[e * GB + r] = L.d[e0 + e];
+            xi[e * GB + r] = L.i[e0 + e];
+          }
+          mbar_arrive(&S.xfull[q]);
+        } else {
+          if (!wwait(&S.xfull[q], xr & 1)) {
+            ok = false;
+            break;
+          }
 #pragma unroll 1
-        for (int u = 0; u < m; ++u) L.offer(mybd[u * 256], mybi[u * 256]);
+          for (int e = 0; e < XE; ++e) L.offer(xd[e * GB + r], xi[e * GB + r]);
+          mbar_arrive(&S.xempty[q]);
+        }
       }
-      if (rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&S.tempty[buf]);
-        mbar_arrive(&S.mempty[sl]);
-      }
+      if (ok && h == 0 && rowok) L.store(a.ldist + (size_t)ip * KP, a.lidx + (size_t)ip * KP);
     }
   }
   // teardown: the last commit completes before tensor memory is freed
@@ -586,14 +838,70 @@ __global__ void __launch_bounds__(256, 6) rerank_kernel(const float* __restrict_
   }
 }
 
-size_t gram_smem(int N, int dp) {
-  (void)dp;
-  return (size_t)STAGES * N * 128 + (size_t)NSLOT * (N + 32) * 8 + (size_t)256 * 32 * 8 + sizeof(PersistSmem) + 1024;
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct GramPlan {
+  int ok = 0;
+  int rowb = 0, nk = 0, stages = 0;
+  uint32_t a_off = 0, b_off = 0, slot_off = 0, x_off = 0, bar_off = 0, b_stage_bytes = 0;
+  size_t smem = 0;
+};
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 227 * 1024;
+  }
+  return v;
 }
 
-template <int KP>
-int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
-  if (cudaFuncSetAttribute((const void*)gram_window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// Shared-memory layout for the widest window wmax of a launch.
+GramPlan gram_plan(int d, int wmax, bool f8, int smem_cap) {
+  GramPlan p;
+  p.rowb = f8 ? (d + 127) / 128 * 128 : (d + 63) / 64 * 128;
+  p.nk = p.rowb / 128;
+  if (wmax < 1 || p.nk > 32) return p;
+  const int W8 = (wmax + 7) & ~7;
+  const int ncol = GB + 2 * W8;
+  const int J = (ncol + SLOT_COLS - 1) / SLOT_COLS;
+  const int stage_rows = J == 1 ? ncol : SLOT_COLS;
+  p.b_stage_bytes = (uint32_t)stage_rows * 128u;
+  const size_t a_bytes = J > 1 ? (size_t)p.nk * GB * 128 : 0;
+  const size_t ent = f8 ? 16 : 8;
+  const size_t slot_bytes = (size_t)NSLOT * SLOT_ENTS * ent;
+  const size_t x_bytes = (size_t)2 * XE * GB * 4;
+  const size_t bar_bytes = (sizeof(Bars) + 127) / 128 * 128;
+  size_t off = 0;
+  p.a_off = (uint32_t)off;
+  off += a_bytes;
+  p.b_off = (uint32_t)off;  // 1024-aligned: a_bytes is a multiple of 16 KB
+  const size_t fixed = a_bytes + slot_bytes + x_bytes + bar_bytes + 1024;
+  if ((size_t)smem_cap <= fixed) return p;
+  int st = (int)(((size_t)smem_cap - fixed) / p.b_stage_bytes);
+  if (st > MAX_STAGES) st = MAX_STAGES;
+  if (st < 2) return p;
+  p.stages = st;
+  off += (size_t)st * p.b_stage_bytes;
+  p.slot_off = (uint32_t)off;
+  off += slot_bytes;
+  p.x_off = (uint32_t)off;
+  off += x_bytes;
+  p.bar_off = (uint32_t)off;
+  off += bar_bytes;
+  p.smem = off + 1024;
+  // one block per SM: it holds all 512 tensor-memory columns, so it also asks
+  // for more than half of the SM's shared memory
+  if (p.smem < 120 * 1024) p.smem = 120 * 1024;
+  p.ok = 1;
+  return p;
+}
+
+template <int KP, bool F8>
+int launch_band(const GramArgs& a, size_t smem, cudaStream_t s) {
+  if (cudaFuncSetAttribute((const void*)gram_band_kernel<KP, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
   int sms = 152;
@@ -601,55 +909,64 @@ int launch_gram_kp(const GramArgs& a, size_t smem, cudaStream_t s) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  gram_window_kernel<KP><<<grid, PT, smem, s>>>(a);
-  hf_after_launch("gram_window_kernel", s);
+  gram_band_kernel<KP, F8><<<grid, PT, smem, s>>>(a);
+  hf_after_launch(F8 ? "gram_band_kernel<fp8>" : "gram_band_kernel<bf16>", s);
   return HF_OK;
 }
 
 }  // namespace
 
-int gram_supported(int d, int w) {
-  const int dp = (d + KC - 1) / KC * KC;
-  const int W8 = (w + 7) / 8 * 8;
-  const int N = GB + 2 * W8;
-  return W8 <= 64 && N * 8 <= 16 * LW * 32 && gram_smem(N, dp) <= 220 * 1024;
+int gram_supported(int d, int w, int form) {
+  if (form != 1 && form != 2) return 0;
+  return gram_plan(d, w, form == 2, max_smem_optin()).ok;
 }
 
-void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s) {
-  const int dp = (d + KC - 1) / KC * KC;
-  prepare_bf16_kernel<<<hf_blocks(n * 32, 256, 152 * 16), 256, 0, s>>>(x, n, d, dp,
-                                                                      static_cast<__nv_bfloat16*>(xb), nrm);
-  hf_after_launch("prepare_bf16_kernel", s);
+size_t gram_row_bytes(int d, int form) { return form == 2 ? (size_t)(d + 127) / 128 * 128 : (size_t)(d + 63) / 64 * 128; }
+
+void launch_prepare_operands(const float* x, int64_t n, int d, int form, void* xq, float2* meta, cudaStream_t s) {
+  const unsigned blocks = hf_blocks(n * 32, 256, 152 * 16);
+  if (form == 2) {
+    prepare_fp8_kernel<<<blocks, 256, 0, s>>>(x, n, d, (int)gram_row_bytes(d, 2), static_cast<uint8_t*>(xq), meta);
+    hf_after_launch("prepare_fp8_kernel", s);
+  } else {
+    prepare_bf16_kernel<<<blocks, 256, 0, s>>>(x, n, d, (int)gram_row_bytes(d, 1) / 2,
+                                               static_cast<__nv_bfloat16*>(xq), meta);
+    hf_after_launch("prepare_bf16_kernel", s);
+  }
 }
 
-size_t bf16_pitch(int d) { return (size_t)(d + KC - 1) / KC * KC; }
-
-int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const uint32_t* sigma, int w, int kp,
-                       uint32_t* li, float* ld, int* err, cudaStream_t s) {
+int launch_gram_window(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma, int w,
+                       const int32_t* tile_w, const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err,
+                       cudaStream_t s) {
+  const bool f8 = form == 2;
+  const GramPlan p = gram_plan(d, w, f8, max_smem_optin());
+  if (!p.ok) return HF_EINVAL;
   GramArgs a;
-  a.xb = static_cast<const __nv_bfloat16*>(xb);
-  a.nrm = nrm;
+  a.xq = static_cast<const uint8_t*>(xq);
+  a.meta = meta;
   a.sigma = sigma;
+  a.tile_w = tile_w;
+  a.pw = pw;
   a.n = n;
-  a.dp = (int)bf16_pitch(d);
+  a.rowb = p.rowb;
+  a.nk = p.nk;
   a.w = w;
-  a.W8 = (w + 7) / 8 * 8;
-  a.N = GB + 2 * a.W8;
-  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
-  // K-major, N >> 3 at bit 17, M >> 4 at bit 24
-  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.N >> 3) << 17) | ((uint32_t)(GB >> 4) << 24);
+  a.stages = p.stages;
+  a.a_off = p.a_off;
+  a.b_off = p.b_off;
+  a.slot_off = p.slot_off;
+  a.x_off = p.x_off;
+  a.bar_off = p.bar_off;
+  a.b_stage_bytes = p.b_stage_bytes;
   a.lidx = li;
   a.ldist = ld;
   a.err = err;
   a.spin_limit = 2000000000ull;  // 2 s per wait (globaltimer nanoseconds)
-  // one block per SM (it holds all 512 tensor-memory columns): each block asks
-  // for more than half of the SM's shared memory
-  size_t smem = gram_smem(a.N, a.dp);
-  if (smem < 120 * 1024) smem = 120 * 1024;
-  switch (kp) {
-    case 16: return launch_gram_kp<16>(a, smem, s);
-    case 32: return launch_gram_kp<32>(a, smem, s);
-    case 64: return launch_gram_kp<64>(a, smem, s);
+  switch (kp * 2 + (f8 ? 1 : 0)) {
+    case 32: return launch_band<16, false>(a, p.smem, s);
+    case 33: return launch_band<16, true>(a, p.smem, s);
+    case 64: return launch_band<32, false>(a, p.smem, s);
+    case 65: return launch_band<32, true>(a, p.smem, s);
     default: return HF_EINVAL;
   }
 }

@@ -19,6 +19,9 @@ enum : int {
 
 __device__ __forceinline__ void hf_raise(int* err, int bit) { atomicOr(err, bit); }
 
+// Slots of hf_get_timings (phase milliseconds and a few per-call figures).
+constexpr int HF_NTIMINGS = 12;
+
 // ---------------------------------------------------------------------------
 // The forest handle.
 // ---------------------------------------------------------------------------
@@ -60,10 +63,11 @@ struct hf_forest {
 
   int* err = nullptr;         // device error word
 
-  // tensor mode: BF16 copy of the points (pitch bf16_pitch(d)) and the FP32
-  // squared norms of its rows, made on first use
+  // tensor mode: operand copy of the points (BF16 or e4m3 rows, pitch
+  // gram_row_bytes) and per point (squared norm, scale), made on first use
   void* xb = nullptr;
-  float* xnrm = nullptr;
+  float2* xmeta = nullptr;
+  int xform = 0;  // form of xb: 0 none, 1 BF16, 2 FP8
 
   uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
   uint32_t* p0t = nullptr;    // [ceil(n/32)][d] bit-sliced plane 0 (scratch, top-level prefix path)
@@ -79,7 +83,7 @@ struct hf_forest {
   int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
   int timing = 1;
 
-  float timings[8] = {0};
+  float timings[HF_NTIMINGS] = {0};
 };
 
 // ---------------------------------------------------------------------------
@@ -120,12 +124,17 @@ int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s);
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
 
-// gram.cu
-int gram_supported(int d, int w);
-size_t bf16_pitch(int d);
-void launch_prepare_bf16(const float* x, int64_t n, int d, void* xb, float* nrm, cudaStream_t s);
-int launch_gram_window(const void* xb, const float* nrm, int64_t n, int d, const uint32_t* sigma, int w, int kp,
-                       uint32_t* li, float* ld, int* err, cudaStream_t s);
+// gram.cu -- tensor-core window distances. form 1: BF16 operands; form 2:
+// FP8 e4m3 operands with one scale per vector.
+int gram_supported(int d, int w, int form);
+size_t gram_row_bytes(int d, int form);  // operand row pitch in bytes
+// operand rows (n x gram_row_bytes) and per point (squared norm, scale)
+void launch_prepare_operands(const float* x, int64_t n, int d, int form, void* xq, float2* meta, cudaStream_t s);
+// one tree: tile_w (per tile of 128 positions, this tree's window) and pw
+// (per point window) may be null, then every point uses w
+int launch_gram_window(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma, int w,
+                       const int32_t* tile_w, const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err,
+                       cudaStream_t s);
 int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
                   cudaStream_t s);
 
@@ -136,6 +145,13 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
 
 // host helpers (api.cu)
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);
+// Device memory from the library's stream-ordered pool (allocated and freed
+// in order on s).
+cudaError_t hf_dalloc_bytes(void** p, size_t bytes, cudaStream_t s);
+void hf_dfree_bytes(void* p, cudaStream_t s);
+// Synchronises s, reads and clears the forest's error word and maps it (and
+// any CUDA error) to a status code; every entry point ends with it.
+int hf_finish(hf_forest* f, cudaStream_t s);
 
 // With HF_DEBUG=1 in the environment: synchronise `s` after a launch and print
 // the kernel's name and any CUDA error to stderr (a no-op otherwise).

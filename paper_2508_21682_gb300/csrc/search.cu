@@ -515,15 +515,7 @@ extern "C" int hf_search_static(hf_forest* f, const float* queries, int64_t nq, 
   cudaGetLastError();  // an earlier call's error was reported by that call
   launch_quantize_codes(queries, nq, f->d, f->lo, f->scale, f->bits, qc, f->err, s);
   rc = launch_search(f, queries, qc, nq, k, w, reinterpret_cast<uint32_t*>(out_idx), out_dist, nullptr, -1, s);
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) return HF_ECUDA;
-  if (rc != HF_OK) return rc;
-  int word = 0;
-  if (cudaMemcpy(&word, f->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return HF_ECUDA;
-  if (word) {
-    cudaMemset(f->err, 0, sizeof(int));
-    return (word & HF_ERRBIT_NONFINITE) ? HF_ENONFINITE : HF_ETIMEOUT;
-  }
-  return HF_OK;
+  // the same synchronisation and status mapping as every other entry point
+  const int rc2 = hf_finish(f, s);
+  return rc != HF_OK ? rc : rc2;
 }

@@ -705,32 +705,44 @@ int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {
   uint8_t* ys = nullptr;
   uint2* druns = f->tie.big_runs + (size_t)t * f->tie.big_cap;
   int rc = HF_OK;
-  if (cudaMalloc(&fk, (size_t)total * W * 8) != cudaSuccess || cudaMalloc(&pt, total * 4) != cudaSuccess ||
-      cudaMalloc(&rn, total * 4) != cudaSuccess || cudaMalloc(&ord, (size_t)m * 4) != cudaSuccess ||
-      cudaMalloc(&doffs, nbig * 4) != cudaSuccess ||
-      cudaMalloc(&ys, (size_t)nbig * tt * f->d) != cudaSuccess) {
-    rc = HF_ENOMEM;
-  } else {
+  auto take = [&](void** p, size_t bytes) {
+    if (rc == HF_OK && hf_dalloc_bytes(p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      rc = HF_ENOMEM;
+    }
+  };
+  take((void**)&fk, (size_t)total * W * 8);
+  take((void**)&pt, total * 4);
+  take((void**)&rn, total * 4);
+  take((void**)&ord, (size_t)m * 4);
+  take((void**)&doffs, nbig * 4);
+  take((void**)&ys, (size_t)nbig * tt * f->d);
+  if (rc == HF_OK) {
     cudaMemcpyAsync(doffs, offs.data(), nbig * 4, cudaMemcpyHostToDevice, s);
     uint32_t* sig = f->sigma + (size_t)t * n;
     big_fill_kernel<<<nbig, tt, 0, s>>>(f->planes, n, f->d, f->W32, f->bits, W, f->pi + (size_t)t * f->d,
                                         f->rbits + (size_t)t * f->W32, druns, doffs, (int)nbig, sig, fk, pt,
-                                        rn, ys); hf_after_launch("big_fill_kernel", s);
-    iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m); hf_after_launch("iota_kernel", s);
+                                        rn, ys);
+    hf_after_launch("big_fill_kernel", s);
+    iota_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m);
+    hf_after_launch("iota_kernel", s);
     for (uint32_t kk = 2; kk <= m; kk <<= 1)
       for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
         bitonic_step_kernel<<<hf_blocks(m, 256), 256, 0, s>>>(ord, m, j, kk, fk, pt, rn, W, (uint32_t)total);
         hf_after_launch("bitonic_step_kernel", s);
       }
-    big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig); hf_after_launch("big_write_kernel", s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = HF_ECUDA;
+    big_write_kernel<<<hf_blocks(total, 256), 256, 0, s>>>(ord, (uint32_t)total, pt, rn, druns, doffs, sig);
+    hf_after_launch("big_write_kernel", s);
   }
-  cudaFree(fk);
-  cudaFree(pt);
-  cudaFree(rn);
-  cudaFree(ord);
-  cudaFree(doffs);
-  cudaFree(ys);
+  // stream-ordered frees: the pool hands the memory to the next user of s
+  // without a device-wide synchronisation
+  hf_dfree_bytes(fk, s);
+  hf_dfree_bytes(pt, s);
+  hf_dfree_bytes(rn, s);
+  hf_dfree_bytes(ord, s);
+  hf_dfree_bytes(doffs, s);
+  hf_dfree_bytes(ys, s);
+  if (rc == HF_OK && cudaGetLastError() != cudaSuccess) rc = HF_ECUDA;
   return rc;
 }
 

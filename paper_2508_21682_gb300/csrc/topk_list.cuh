@@ -42,6 +42,14 @@ struct ListK {
       *reinterpret_cast<uint4*>(gi + j) = make_uint4(i[j], i[j + 1], i[j + 2], i[j + 3]);
     }
   }
+  // Every slot empty: (+inf, 0xffffffff).
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      d[j] = INFINITY;
+      i[j] = 0xffffffffu;
+    }
+  }
   // Inserts (cd, ci) unless it is no better than the last slot or listed.
   __device__ __forceinline__ void offer(float cd, uint32_t ci) {
     if (!lessp(cd, ci, d[KP - 1], i[KP - 1])) return;

@@ -34,13 +34,15 @@
 
 namespace {
 
-constexpr int WNT = 256;        // threads per block = units per block
+// Threads per block = units per block: 256 for bands up to offset 480 and
+// 512 (two blocks' worth of unit rows) beyond, where B = ROWS - dhi would
+// otherwise fall below 32 owned positions.
 constexpr int DC = 16;          // coordinates per staged chunk
 constexpr int UR = 8;           // rows per unit
 constexpr int UC = 8;           // offsets per unit
 constexpr int WB = 32;          // offsets per band (launch)
-constexpr int ROWS = 512;       // unit rows per block: B + dhi
 constexpr int OG = WB / UC;     // offset groups per band
+__host__ __device__ constexpr int rows_of(int nt) { return nt * UR * UC / WB; }  // unit rows: B + dhi
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
@@ -72,7 +74,7 @@ __device__ __forceinline__ int rslot(int r) {
 // Lanes take 16 consecutive coordinates of 2 rows: 64-byte global segments.
 __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const uint32_t* srow,
                                             const float* __restrict__ x, int d, int c0) {
-  for (int e = threadIdx.x; e < NR * DC; e += WNT) {
+  for (int e = threadIdx.x; e < NR * DC; e += blockDim.x) {
     const int r = e >> 4, c = e & (DC - 1);
     const uint32_t pid = srow[r];
     const bool ok = pid != 0xffffffffu && c0 + c < d;
@@ -84,10 +86,11 @@ __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const u
 
 
 // One band of offsets [dlo, dlo + WB - 1] for the block's positions.
-template <int KP>
-__global__ void __launch_bounds__(WNT, 2)
+template <int KP, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT)
 window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sigma, int w,
               int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
+  constexpr int ROWS = rows_of(NT);
   extern __shared__ __align__(16) float smem[];
   const int dhi = dlo + WB - 1;
   const int NR = B + 2 * dhi;  // staged rows
@@ -100,7 +103,7 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
 
   const int64_t s = (int64_t)blockIdx.x * B;
   const int64_t r0 = s - dhi;  // position of staged row 0
-  for (int r = threadIdx.x; r < NR; r += WNT) {
+  for (int r = threadIdx.x; r < NR; r += NT) {
     const int64_t p = r0 + r;
     srow[r] = (p >= 0 && p < n) ? __ldg(sigma + p) : 0xffffffffu;
   }
@@ -158,7 +161,7 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
 
   // merge: positions s + tt, tt < B; the point's list is held in registers
   const int wtop = min(dhi, w);
-  for (int tt = threadIdx.x; tt < B; tt += WNT) {
+  for (int tt = threadIdx.x; tt < B; tt += NT) {
     const int64_t p = s + tt;
     if (p >= n) break;
     const int rowp = tt + dhi;  // staged row of p
@@ -182,11 +185,26 @@ __global__ void list_init_kernel(uint32_t* __restrict__ idx, float* __restrict__
   }
 }
 
-size_t window_smem(int B, int dhi) {
+size_t window_smem(int B, int dhi, int rows) {
   const int NR = B + 2 * dhi;
   const size_t staging = (size_t)2 * DC * staging_pitch((NR + 7) & ~7);
-  const size_t bandf = (size_t)ROWS * WB;
+  const size_t bandf = (size_t)rows * WB;
   return ((staging > bandf ? staging : bandf) + (size_t)NR) * 4;
+}
+
+template <int KP, int NT>
+int launch_band(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int dlo, uint32_t* li, float* ldd,
+                cudaStream_t s) {
+  const int dhi = dlo + WB - 1;
+  const int B = rows_of(NT) - dhi;
+  const size_t smem = window_smem(B, dhi, rows_of(NT));
+  if (B < 32 || smem > 227 * 1024) return HF_ENOTIMPL;
+  if (cudaFuncSetAttribute((const void*)window_kernel<KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return HF_ECUDA;
+  window_kernel<KP, NT><<<hf_blocks(n, B), NT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
+  hf_after_launch("window_kernel", s);
+  return HF_OK;
 }
 
 template <int KP>
@@ -194,15 +212,9 @@ int launch_kp(const float* x, int64_t n, int d, const uint32_t* sigma, int w, ui
               cudaStream_t s) {
   for (int dlo = 1; dlo <= w; dlo += WB) {
     const int dhi = dlo + WB - 1;
-    const int B = ROWS - dhi;
-    if (B < 32) return HF_ENOTIMPL;
-    const size_t smem = window_smem(B, dhi);
-    if (smem > 227 * 1024) return HF_ENOTIMPL;
-    if (cudaFuncSetAttribute((const void*)window_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return HF_ECUDA;
-    window_kernel<KP><<<hf_blocks(n, B), WNT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
-    hf_after_launch("window_kernel", s);
+    const int rc = rows_of(256) - dhi >= 32 ? launch_band<KP, 256>(x, n, d, sigma, w, dlo, li, ldd, s)
+                                            : launch_band<KP, 512>(x, n, d, sigma, w, dlo, li, ldd, s);
+    if (rc != HF_OK) return rc;
   }
   return HF_OK;
 }
@@ -216,8 +228,9 @@ void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s)
 
 int window_list_pitch(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
 
-// One launch per band of 32 offsets; w up to 448 (B >= 32). Lists have
-// window_list_pitch(k) slots per point.
+// One launch per band of 32 offsets; w up to HF_PLAIN_MAX_W (B >= 32 and
+// the staging within shared memory). Lists have window_list_pitch(k) slots
+// per point.
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s) {
   switch (kp) {

@@ -70,3 +70,35 @@ def check_lists(x, gi, gd, oi, od, owners=None, queries=None, cand=None, rtol=RT
     eq = np.mean(np.all(gi == oi, axis=1))
     assert eq >= min_equal, f"only {eq:.4f} of rows identical"
     return eq
+
+
+def check_tensor_lists(x, gi, gd, oi, owners, cand=None, rtol=RTOL, min_hit=0.995):
+    """Checks of the tensor form (tensor-core distance estimates pick each
+    point's best k + slack candidates, an exact float32 re-rank orders them).
+
+    Every returned distance must be the exact distance of its pair within
+    rtol; lists ascend by (distance, index), hold no repeats and never the
+    owner; every pick is one of the owner's window candidates (when `cand` is
+    given); the filled-slot pattern equals the oracle's; and at least
+    `min_hit` of the oracle's top-k entries are found (the estimate may drop a
+    true top-k candidate out of the k + slack kept, rarely)."""
+    gi = np.asarray(gi).astype(np.int64)
+    gd = np.asarray(gd).astype(np.float64)
+    valid = gi >= 0
+    assert np.array_equal(valid, oi >= 0), "filled-slot pattern differs from the oracle"
+    true = fp64_dist(x, np.broadcast_to(owners[:, None], gi.shape), np.where(valid, gi, -1))
+    err = np.abs(gd[valid] - true[valid])
+    assert np.all(err <= rtol * true[valid] + 1e-30), f"max rel err {np.max(err / np.maximum(true[valid], 1e-30))}"
+    assert np.all(np.isinf(gd[~valid])), "unfilled slots must hold +inf"
+    for r in range(gi.shape[0]):
+        row = gi[r][valid[r]]
+        assert len(set(row.tolist())) == len(row), f"repeat in row {r}"
+        assert owners[r] not in set(row.tolist()), f"self in row {r}"
+        if cand is not None:
+            assert set(row.tolist()) <= set(cand[r][cand[r] >= 0].tolist()), f"row {r} holds a non-candidate"
+        dd = gd[r][valid[r]]
+        assert np.all((dd[1:] > dd[:-1]) | ((dd[1:] == dd[:-1]) & (row[1:] > row[:-1]))), f"row {r} order"
+    hits = sum(len(set(a[a >= 0].tolist()) & set(b[b >= 0].tolist())) for a, b in zip(gi, oi))
+    hit = hits / max(1, int((oi >= 0).sum()))
+    assert hit >= min_hit, f"found {hit:.5f} of the oracle's top-k"
+    return hit

@@ -13,7 +13,7 @@ import pytest
 
 import oracle as O
 import synthdata as S
-from _helpers import check_lists
+from _helpers import check_lists, check_tensor_lists
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -40,10 +40,17 @@ def full(hf):
     G = hf.build(xd, T=T, bits=8, seed=S.SEED_FOREST)
     gi, gd = G.knn_graph(K, W)
     si, sd = G.search(torch.from_numpy(q).cuda(), K, W)
+    # the tensor form on the same forest, at the bench's window and at the
+    # widest single-tile window (w = 64)
+    G.set_option("mode", 1)
+    ti, td = G.knn_graph(K, W)
+    ti64, td64 = G.knn_graph(K, 64)
+    G.set_option("mode", 0)
     torch.cuda.synchronize()
     orders = [G.order(t).astype(np.int64) for t in range(T)]
     res = dict(x=x, q=q, G=G, gi=gi.cpu().numpy(), gd=gd.cpu().numpy(), si=si.cpu().numpy(),
-               sd=sd.cpu().numpy(), orders=orders)
+               sd=sd.cpu().numpy(), orders=orders, ti=ti.cpu().numpy(), td=td.cpu().numpy(),
+               ti64=ti64.cpu().numpy(), td64=td64.cpu().numpy())
     yield res
     G.close()
 
@@ -93,13 +100,14 @@ def window_rows(orders, pts, w):
     """Window candidates of points `pts` in the given (checked) orders."""
     out = []
     for sig in orders:
-        inv = np.empty(N, np.int64)
-        inv[sig] = np.arange(N)
+        n = sig.shape[0]
+        inv = np.empty(n, np.int64)
+        inv[sig] = np.arange(n)
         p = inv[pts]
         c = np.full((len(pts), 2 * w), -1, np.int64)
         for j, off in enumerate(list(range(-w, 0)) + list(range(1, w + 1))):
             pp = p + off
-            ok = (pp >= 0) & (pp < N)
+            ok = (pp >= 0) & (pp < n)
             c[ok, j] = sig[pp[ok]]
         out.append(c)
     return np.concatenate(out, axis=1)
@@ -111,6 +119,20 @@ def test_sampled_graph_rows(full):
     cand = window_rows(full["orders"], pts, W)
     oi, od = O.topk_from_candidates(full["x"], pts, cand, K)
     check_lists(full["x"], full["gi"][pts], full["gd"][pts], oi, od, owners=pts, cand=cand)
+
+
+@pytest.mark.parametrize("w,key", [(W, "ti"), (64, "ti64")])
+def test_tensor_sampled_graph_rows(full, w, key):
+    """The tensor form at 3M x 384 (about 154 tiles per persistent block, so
+    every ring, accumulator and barrier phase wraps many times): sampled rows
+    against the oracle's top-k of their window candidates."""
+    rng = np.random.default_rng(S.SEED_SAMPLE + 2)
+    pts = np.sort(np.concatenate([rng.choice(N, 1500, replace=False), np.arange(N - 40, N), np.arange(40)]))
+    pts = np.unique(pts)
+    cand = window_rows(full["orders"], pts, w)
+    oi, od = O.topk_from_candidates(full["x"], pts, cand, K)
+    ti, td = full[key], full["td" if key == "ti" else "td64"]
+    check_tensor_lists(full["x"], ti[pts], td[pts], oi, owners=pts, cand=cand)
 
 
 def test_sampled_search_rows(full):
@@ -160,4 +182,50 @@ def test_exact_oracle_200k(hf):
     cand = O.candidate_sets(F, W)[rows]
     oi, od = O.topk_from_candidates(x, rows, cand, K)
     check_lists(x, gi.cpu().numpy()[rows], gd.cpu().numpy()[rows], oi, od, owners=rows, cand=cand)
+    G.close()
+
+
+def test_tensor_exact_oracle_200k(hf):
+    """The tensor form against the oracle end to end at 200,000 x 384, T = 2,
+    w = 32, k = 15: about 1,563 tiles, ten or more per persistent block."""
+    n, T2 = 200_000, 2
+    x = S.gaussian_mixture(n, D, n_components=1000, seed=S.SEED_DATA)
+    F = O.Forest(x, T=T2, bits=8, seed=S.SEED_FOREST)
+    G = hf.build(torch.from_numpy(x).cuda(), T=T2, bits=8, seed=S.SEED_FOREST)
+    G.set_option("mode", 1)
+    gi, gd = G.knn_graph(K, W)
+    oi, od = O.knn_graph(F, K, W)
+    cand = O.candidate_sets(F, W)
+    check_tensor_lists(x, gi.cpu().numpy(), gd.cpu().numpy(), oi, owners=np.arange(n), cand=cand)
+    G.close()
+
+
+def test_tensor_ragged_1m_w64(hf):
+    """A ragged n (1,000,003 = 7,812 tiles + 67 rows) at the widest
+    single-tile window: sampled rows, the last tile's rows included."""
+    n, T2, w = 1_000_003, 2, 64
+    x = S.gaussian_mixture(n, D, n_components=1000, seed=S.SEED_DATA + 7)
+    G = hf.build(torch.from_numpy(x).cuda(), T=T2, bits=8, seed=S.SEED_FOREST)
+    G.set_option("mode", 1)
+    gi, gd = G.knn_graph(K, w)
+    torch.cuda.synchronize()
+    orders = [G.order(t).astype(np.int64) for t in range(T2)]
+    lo, sc = oracle_setup(x)
+    for t in range(T2):
+        pi, r = O.tree_params(S.SEED_FOREST, t, D)
+        sig = orders[t]
+        assert np.array_equal(np.sort(sig), np.arange(n))
+        # order property on the tail and on sampled positions
+        pos = np.concatenate([np.arange(n - 200, n - 1), np.random.default_rng(t).choice(n - 1, 2000, replace=False)])
+        ka = O.hilbert_keys(O.quantize(x[sig[pos]], lo, sc, 8), pi, r, 8)
+        kb = O.hilbert_keys(O.quantize(x[sig[pos + 1]], lo, sc, 8), pi, r, 8)
+        for i in range(len(pos)):
+            ta = tuple(int(v) for v in ka[i]) + (int(sig[pos[i]]),)
+            tb = tuple(int(v) for v in kb[i]) + (int(sig[pos[i] + 1]),)
+            assert ta < tb
+    rng = np.random.default_rng(S.SEED_SAMPLE + 3)
+    pts = np.unique(np.concatenate([rng.choice(n, 1500, replace=False), orders[0][-67:], orders[1][-67:]]))
+    cand = window_rows(orders, pts, w)
+    oi, od = O.topk_from_candidates(x, pts, cand, K)
+    check_tensor_lists(x, gi.cpu().numpy()[pts], gd.cpu().numpy()[pts], oi, owners=pts, cand=cand)
     G.close()

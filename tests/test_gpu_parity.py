@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import synthdata as S
-from _helpers import RTOL, check_lists
+from _helpers import RTOL, check_lists, check_tensor_lists
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -113,7 +113,8 @@ def test_host_input_and_output_buffers(hf):
     (20000, 16, 8, 16, 10, False),   # tiny config as specified
     (4001, 384, 2, 32, 15, True),    # full-size shape, small n, ragged tail
     (3007, 64, 3, 60, 12, True),     # w not a multiple of 8, two passes of units
-    (2003, 24, 2, 128, 20, False),   # widest window of one pass
+    (2003, 24, 2, 128, 20, False),   # four bands of 32 offsets
+    (3001, 24, 2, 520, 10, False),   # bands past offset 480: 512-thread blocks
     (50, 8, 3, 40, 10, False),       # n < 2w + 1
     (12, 5, 2, 3, 15, False),        # k > n - 1: padded slots
     (3000, 3, 1, 5, 5, False),       # T = 1, d not a multiple of 4
@@ -212,42 +213,63 @@ def test_invalid_graph_arguments(hf):
         with pytest.raises(hf.HFError) as e:
             G.knn_graph(k, w)
         assert e.value.status == hf.HF_EINVAL
+    with pytest.raises(hf.HFError) as e:  # wider than the plain form covers
+        G.knn_graph(5, 705)
+    assert e.value.status == hf.HF_ENOTIMPL
     G.close()
 
 
 # ---------------------------------------------------------------- tensor mode
-@pytest.mark.parametrize("n,d,T,w,k,mixture", [
-    (20000, 16, 8, 16, 10, False),   # tiny config
-    (6001, 384, 2, 32, 15, True),    # full-size shape, ragged tail (6001 = 46 tiles + 113)
-    (3007, 64, 3, 60, 12, True),     # w not a multiple of 8
-    (50, 8, 3, 40, 10, False),       # n < 2w + 1: one tile, mostly empty columns
-    (3000, 100, 2, 7, 5, False),     # d not a multiple of 64 (zero-padded K)
+# min_hit: the share of the oracle's top-k that the form must find. BF16
+# estimates keep k + 1 and find >= 0.995; FP8 e4m3 estimates (3 mantissa
+# bits, a dot-product error near 1.5e-3 on unit vectors) drop true neighbours
+# that lie within that error of the k + slack boundary, more often the more
+# candidates a point has: measured 0.990 at w = 32 and 0.944 at w = 300 with
+# k + 17 kept.
+@pytest.mark.parametrize("n,d,T,w,k,mixture,mode,slack,min_hit", [
+    (20000, 16, 8, 16, 10, False, 1, -1, 0.995),    # tiny config
+    (6001, 384, 2, 32, 15, True, 1, -1, 0.995),     # full-size shape, ragged tail (6001 = 46 tiles + 113)
+    (3007, 64, 3, 60, 12, True, 1, -1, 0.995),      # w not a multiple of 8
+    (50, 8, 3, 40, 10, False, 1, -1, 0.995),        # n < 2w + 1: one tile, mostly empty columns
+    (3000, 100, 2, 7, 5, False, 1, -1, 0.995),      # d not a multiple of 64 (zero-padded K)
+    (5003, 384, 2, 100, 15, True, 1, -1, 0.995),    # two column units (resident own rows)
+    (4001, 200, 2, 300, 10, True, 1, -1, 0.995),    # three units, the last one narrow (N = 96)
+    (3001, 384, 2, 512, 15, True, 1, -1, 0.995),    # the widest window of the bench (five units)
+    (700, 48, 2, 500, 9, False, 1, -1, 0.995),      # w > n: every unit partly outside the matrix
+    (6001, 384, 2, 32, 15, True, 2, 17, 0.98),      # FP8 e4m3 operands, one unit
+    (5003, 384, 2, 300, 15, True, 2, 17, 0.93),     # FP8, three units
+    (20000, 16, 4, 16, 10, False, 2, 22, 0.98),     # FP8 at d = 16 (one K chunk)
 ])
-def test_tensor_mode_graph(hf, n, d, T, w, k, mixture):
-    """BF16 Gram tiles pick each point's best 2k candidates, the exact float32
-    re-rank orders them: distances must be exact (1e-5) and the lists may
-    differ from the oracle only where the BF16 estimate dropped a true top-k
-    candidate out of the best 2k (rare)."""
+def test_tensor_mode_graph(hf, n, d, T, w, k, mixture, mode, slack, min_hit):
+    """Tensor-core distance estimates (mode 1: BF16, mode 2: FP8 e4m3 with a
+    scale per vector) pick each point's best k + slack candidates, the exact
+    float32 re-rank orders them: distances must be exact (1e-5) and the lists
+    may differ from the oracle only where the estimate dropped a true top-k
+    candidate out of the k + slack kept."""
     x = S.gaussian_mixture(n, d, n_components=30, seed=2) if mixture else S.unit_gaussian(n, d, seed=2)
     G, F = build_both(hf, x, T, 8)
-    G.set_option("mode", 1)
+    G.set_option("mode", mode)
+    G.set_option("tensor_slack", slack)
     gi, gd = G.knn_graph(k, w)
+    assert G.timings()["graph_form"] == mode, "the tensor form must run, not the plain fallback"
     gi, gd = gi.cpu().numpy().astype(np.int64), gd.cpu().numpy()
     oi, od = O.knn_graph(F, k, w)
     cand = O.candidate_sets(F, w)
-    owners = np.arange(n)
-    valid = gi >= 0
-    assert np.array_equal(valid, oi >= 0)
-    true = O.sq_dist_fp64(x, np.broadcast_to(owners[:, None], gi.shape), np.where(valid, gi, -1))
-    assert np.all(np.abs(gd[valid] - true[valid]) <= RTOL * true[valid])
-    for r in range(n):
-        row = gi[r][valid[r]]
-        assert len(set(row.tolist())) == len(row) and r not in set(row.tolist())
-        assert set(row.tolist()) <= set(cand[r][cand[r] >= 0].tolist())
-        dd = gd[r][valid[r]]
-        assert np.all((dd[1:] > dd[:-1]) | ((dd[1:] == dd[:-1]) & (row[1:] > row[:-1])))
-    hits = sum(len(set(a[a >= 0].tolist()) & set(b[b >= 0].tolist())) for a, b in zip(gi, oi))
-    assert hits / max(1, int((oi >= 0).sum())) >= 0.995
+    check_tensor_lists(x, gi, gd, oi, owners=np.arange(n), cand=cand, min_hit=min_hit)
+    G.close()
+
+
+def test_tensor_mode_falls_back_when_too_wide(hf):
+    """d = 768 BF16 rows with w > 64 do not fit the resident layout: the call
+    runs the plain form and says so in the timings."""
+    x = S.unit_gaussian(600, 768, seed=4)
+    G = hf.build(cuda(x), T=1, bits=8)
+    G.set_option("mode", 1)
+    G.knn_graph(5, 100)
+    assert G.timings()["graph_form"] == 0
+    G.set_option("mode", 2)  # FP8 rows are half as wide: fits
+    G.knn_graph(5, 100)
+    assert G.timings()["graph_form"] == 2
     G.close()
 
 
