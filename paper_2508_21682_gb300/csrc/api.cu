@@ -517,8 +517,12 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   if (tensor && kp > 32) return HF_ENOTIMPL;  // tensor lists hold at most 32 entries
   uint32_t* li = nullptr;
   float* ldd = nullptr;
+  void* xs = nullptr;  // tensor forms: one tree's rows in its order
+  float2* ms = nullptr;
   cudaError_t e = dalloc(&li, (size_t)n * kp, s);
   if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp, s);
+  if (e == cudaSuccess && tensor) e = dalloc_bytes(&xs, (size_t)n * gram_row_bytes(f->d, form), s);
+  if (e == cudaSuccess && tensor) e = dalloc(&ms, (size_t)n, s);
   if (e == cudaSuccess && tensor && f->xform != form) {
     dfree(f->xb, s);
     dfree(f->xmeta, s);
@@ -533,6 +537,8 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   if (e != cudaSuccess) {
     dfree(li, s);
     dfree(ldd, s);
+    dfree(xs, s);
+    dfree(ms, s);
     return map_cuda(e);
   }
   Timer tm(f, s);
@@ -540,10 +546,14 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   launch_list_init(li, ldd, n * kp, s);
   int rc = HF_OK;
   for (int t = 0; t < f->T && rc == HF_OK; ++t) {
-    if (tensor)
-      rc = launch_gram_window(f->xb, f->xmeta, form, n, f->d, f->sigma + (size_t)t * n, w, nullptr, nullptr, kp, li,
-                              ldd, f->err, s);
-    else
+    if (tensor) {
+      cudaEvent_t g0 = tm.mark();
+      launch_gather_rows(f->xb, f->xmeta, form, n, f->d, f->sigma + (size_t)t * n, xs, ms, s);
+      cudaEvent_t g1 = tm.mark();
+      tm.span(9, g0, g1);
+      rc = launch_gram_window(form, n, f->d, f->sigma + (size_t)t * n, w, nullptr, nullptr, kp, li, ldd, f->err, xs,
+                              ms, s);
+    } else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }
   cudaEvent_t a1 = tm.mark();
@@ -571,9 +581,12 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   if (rc == HF_OK) rc = deliver(out_dist, ldd);
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
-  if (rc == HF_OK) tm.collect({4, 7});
+  f->timings[9] = 0.f;
+  if (rc == HF_OK) tm.collect({4, 7, 9});
   dfree(li, s);
   dfree(ldd, s);
+  dfree(xs, s);
+  dfree(ms, s);
   return rc;
 }
 

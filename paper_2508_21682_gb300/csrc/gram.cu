@@ -33,6 +33,7 @@
 // points, so the expansion's cancellation and the operand rounding never
 // reach the result; the list is re-sorted and the first k columns are the
 // answer.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -206,14 +207,32 @@ __global__ void prepare_fp8_kernel(const float* __restrict__ x, int64_t n, int d
   }
 }
 
+// Rows of the operand copy in the order of one tree: xs[p] = xq[sigma[p]]
+// (rowb bytes each, moved in 16-byte pieces) and ms[p] = meta[sigma[p]], so
+// that the Gram kernel reads every unit's rows as one contiguous range.
+__global__ void gather_rows_kernel(const uint8_t* __restrict__ xq, const float2* __restrict__ meta,
+                                   const uint32_t* __restrict__ sigma, int64_t n, int rowb,
+                                   uint8_t* __restrict__ xs, float2* __restrict__ ms) {
+  const int per = rowb >> 4;  // 16-byte pieces per row
+  const int64_t total = n * per;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / per;
+    const int c = (int)(e - p * per);
+    const uint32_t id = __ldg(sigma + p);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(xq + (size_t)id * rowb) + c);
+    __stcs(reinterpret_cast<uint4*>(xs + (size_t)p * rowb) + c, v);
+    if (c == 0) ms[p] = __ldg(meta + id);
+  }
+}
+
 struct GramArgs {
-  const uint8_t* xq;       // operand rows (BF16 or e4m3), pitch rowb bytes
-  const float2* meta;      // per point (squared norm, scale)
+  const float2* ms;        // per position of this tree: (squared norm, scale)
   const uint32_t* sigma;   // order of this tree: position -> point
   const int32_t* tile_w;   // per-tile window of this tree, or null (uniform w)
   const uint16_t* pw;      // per-point window, or null (uniform w)
   int64_t n;
-  int rowb, nk;            // bytes per row (multiple of 128), K chunks
+  int nk;                  // K chunks of 128 bytes per row
+  int elem_per_chunk;      // 64 (BF16) or 128 (FP8) elements per chunk
   int w;                   // window when tile_w is null
   int stages;              // B ring stages
   uint32_t a_off, b_off, slot_off, x_off, bar_off;  // shared-memory layout
@@ -227,45 +246,59 @@ struct GramArgs {
 // ---------------------------------------------------------------------------
 // Persistent, warp-specialised band kernel. One block per SM loops over row
 // tiles t = blockIdx.x + i * gridDim.x and, within a tile, over its units
-// (unit j = columns [256 j, 256 j + Nj) of the tile's column range).
-//   warps 0..3  loaders: per K chunk of a unit, the unit's rows into the B
-//               ring with 16-byte cp.async copies into the swizzled layout; a
-//               stage is full once every loader's copies have landed
-//               (cp.async.mbarrier.arrive: no loader waits for its copies);
-//   warp 4      MMA issuer (one lane): per unit, all K chunks into one of two
-//               tensor-memory accumulators (256 columns each);
-//   warp 5      prep: per unit, the (norm, scale, id) of its columns (and, for
+// (unit j = columns [256 j, 256 j + Nj) of the tile's column range). The
+// operand rows are in the tree's position order (gather_rows_kernel), so a
+// unit's rows are positions [c_lo + 256 j, c_lo + 256 j + Nj) and the tile's
+// own rows positions [s, s + 128).
+//   warp 0      TMA producer (one lane): per K chunk of a unit, boxes of 32
+//               rows x 128 bytes into the B ring (128-byte swizzle, rows
+//               outside the matrix zero-filled); per tile with several
+//               units, the own rows into the resident A region, chunk kc
+//               once the previous tile's last MMA reading it has completed;
+//   warp 1      MMA issuer (one lane): per unit, all K chunks into one of two
+//               tensor-memory accumulators (256 columns each); it also owns
+//               the tensor-memory allocation;
+//   warp 2      prep: per unit, the (norm, scale, id) of its columns (and, for
 //               the first unit, of the tile's own rows) into one of NSLOT
-//               slots; per tile with several units, the own rows into the
-//               resident A region;
-//   warps 6..13 epilogue: a warp owns tensor-memory lanes 32 (warp % 4) ..
-//               + 31 (tile rows) and, in half h = (warp - 6) / 4, the
+//               slots;
+//   warp 3      idle;
+//   warps 4..11 epilogue: a warp owns tensor-memory lanes 32 (warp % 4) ..
+//               + 31 (tile rows) and, in half h = (warp - 4) / 4, the
 //               32-column chunks of parity h.
 // Every barrier wait is bounded (spin_limit ns of %globaltimer); when one
 // gives up, the block raises the error word, every role leaves, and tensor
 // memory is freed after a bounded wait for MMAs in flight.
 // ---------------------------------------------------------------------------
-constexpr int NSLOT = 4;           // staged (norm, scale, id) units: loaders run ahead
+constexpr int NSLOT = 4;           // staged (norm, scale, id) units: the prep warp runs ahead
 constexpr int SLOT_COLS = 256;     // column entries per slot
 constexpr int SLOT_ENTS = SLOT_COLS + GB;  // + the tile's own rows
 constexpr int XE = 16;             // list entries handed over per exchange round
-constexpr int LW = 4;              // loader warps 0..3
-constexpr int MW = LW;             // MMA warp
-constexpr int PW = LW + 1;         // prep warp: slots and the resident A rows
-constexpr int EW0 = LW + 2;        // first epilogue warp
-constexpr int PT = (LW + 2 + 8) * 32;
+constexpr int TW = 0;              // TMA producer warp
+constexpr int MW = 1;              // MMA warp
+constexpr int PW = 2;              // prep warp
+constexpr int EW0 = 4;             // first epilogue warp
+constexpr int PT = (EW0 + 8) * 32;
 constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
 constexpr int MAX_STAGES = 4;
-constexpr int A_PER = GB * 8 / 32;          // A pieces per prep lane and chunk (32)
-constexpr int B_PER = 256 * 8 / (LW * 32);  // B pieces per loader thread and chunk (16)
+constexpr int BOX_ROWS = 32;       // rows per TMA box
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
-// One arrival on *bar once every cp.async this thread has issued so far has
-// landed (the barrier's expected count includes this thread).
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+// One arrival that also expects `bytes` of asynchronous transfers.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// A 2-D box of the tensor map at (x elements, y rows) into shared memory;
+// completion is counted in bytes on *bar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 struct Bars {
@@ -278,35 +311,24 @@ struct Bars {
   int abort;
 };
 
-// One staged column (or own row): BF16 needs (norm, id), FP8 also the scale.
-struct EntB {
-  float nrm;
-  uint32_t id;
-};
-struct EntF {
-  float nrm, sc;
-  uint32_t id, pad;
+// A slot holds, for SLOT_ENTS entries (the unit's SLOT_COLS columns, then
+// the tile's GB own rows), three arrays: squared norm (+inf outside the
+// matrix), scale (FP8 form only) and point index.
+struct SlotView {
+  float* nrm;
+  float* sc;
+  uint32_t* id;
 };
 template <bool F8>
-struct EntOf {
-  using T = EntB;
-};
-template <>
-struct EntOf<true> {
-  using T = EntF;
-};
-__device__ __forceinline__ void ent_set(EntB& e, float n, float, uint32_t id) {
-  e.nrm = n;
-  e.id = id;
+__device__ __forceinline__ SlotView slot_view(unsigned char* slots, int sl) {
+  constexpr int words = F8 ? 3 : 2;
+  float* b = reinterpret_cast<float*>(slots) + (size_t)sl * words * SLOT_ENTS;
+  SlotView v;
+  v.nrm = b;
+  v.sc = F8 ? b + SLOT_ENTS : nullptr;
+  v.id = reinterpret_cast<uint32_t*>(b + (F8 ? 2 : 1) * SLOT_ENTS);
+  return v;
 }
-__device__ __forceinline__ void ent_set(EntF& e, float n, float s, uint32_t id) {
-  e.nrm = n;
-  e.sc = s;
-  e.id = id;
-  e.pad = 0;
-}
-__device__ __forceinline__ float ent_sc(const EntB&) { return 1.0f; }
-__device__ __forceinline__ float ent_sc(const EntF& e) { return e.sc; }
 
 __device__ __forceinline__ uint64_t gtimer() {
   uint64_t t;
@@ -322,8 +344,9 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, uint64_t l
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   uint32_t it = 0;
+  // try_wait suspends the thread for a while before it reports "not yet",
+  // so the loop does not spin hot
   while (!mbar_try_wait(bar, parity)) {
-    __nanosleep(64);  // leave issue slots to the warps doing work
     if ((++it & 15u) == 0) {
       if (*abort) return false;
       if (gtimer() - t0 > limit_ns) {
@@ -370,13 +393,12 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], int j) {
 }
 
 template <int KP, bool F8>
-__global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
-  using Ent = typename EntOf<F8>::T;
+__global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __grid_constant__ CUtensorMap xmap) {
   extern __shared__ unsigned char smraw[];
   unsigned char* base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char* aregion = base + a.a_off;
   unsigned char* bring = base + a.b_off;
-  Ent* slots = reinterpret_cast<Ent*>(base + a.slot_off);
+  unsigned char* slots = base + a.slot_off;
   float* xd = reinterpret_cast<float*>(base + a.x_off);            // [XE][128] distances
   uint32_t* xi = reinterpret_cast<uint32_t*>(xd + XE * GB);        // [XE][128] indices
   Bars& S = *reinterpret_cast<Bars*>(base + a.bar_off);
@@ -389,11 +411,11 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
   if (warp == MW) tmem_alloc(&S.tslot, TMEM_ALL);
   if (tid == 0) {
     for (int i = 0; i < stages; ++i) {
-      mbar_init(&S.full[i], LW * 32);
+      mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], 1);
     }
     for (int i = 0; i < nk; ++i) {
-      mbar_init(&S.afull[i], 32);
+      mbar_init(&S.afull[i], 1);
       mbar_init(&S.aempty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -417,61 +439,52 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
   const uint32_t tmem = S.tslot;
   volatile int* abort = &S.abort;
 
-  if (warp < LW) {
-    // ---------------- loaders: 128 threads. Each copies its pieces of a
-    // chunk and leaves; the stage's "full" barrier completes once every
-    // loader's copies have landed (cp.async.mbarrier.arrive), so a loader
-    // only ever waits for a stage to be released or for a slot's ids.
-    const int lt = tid;
-    uint32_t it = 0, u = 0;
-    bool ok = true;
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const TileGeom g = tile_geom(a, t);
-      for (int j = 0; j < g.J && ok; ++j, ++u) {
-        const int sl = u % NSLOT;
-        const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
-        if (!pwait(&S.mfull[sl], (u / NSLOT) & 1, lim, abort, a.err)) {
-          ok = false;
-          break;
-        }
-        const Ent* se = slots + sl * SLOT_ENTS;
-        // this thread's pieces: the same (row, 16-byte column) in every chunk
-        const uint8_t* bsrc[B_PER];
-        uint32_t bdst[B_PER];
-        uint32_t bstore = 0, bload = 0;
+  if (warp == TW) {
+    // ---------------- TMA producer (one lane)
+    if (lane == 0) {
+      uint32_t it = 0, auses = 0;
+      bool ok = true;
+      const uint32_t chunk_box = (uint32_t)BOX_ROWS * 128u;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileGeom g = tile_geom(a, t);
+        const int64_t s = t * GB, c_lo = s - g.W8;
+        for (int j = 0; j < g.J && ok; ++j) {
+          const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
+          const int nbox = (nj + BOX_ROWS - 1) / BOX_ROWS;
+          const int y0 = (int)(c_lo + (int64_t)SLOT_COLS * j);
+          const bool useA = g.J > 1 && j == 0;
+          for (int kc = 0; kc < nk; ++kc, ++it) {
+            const int x = kc * a.elem_per_chunk;
+            if (useA) {
+              if (!pwait(&S.aempty[kc], (auses & 1) ^ 1, lim, abort, a.err)) {
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&S.afull[kc], (uint32_t)GB * 128u);
+              const uint32_t d0 = smem_u32(aregion + (size_t)kc * GB * 128);
 #pragma unroll
-        for (int q = 0; q < B_PER; ++q) {
-          const int e = lt + q * LW * 32;
-          const int r = e >> 3, pc = e & 7;
-          const uint32_t pid = r < nj ? se[r].id : 0xffffffffu;
-          bsrc[q] = a.xq + (pid != 0xffffffffu ? (size_t)pid * a.rowb : 0) + pc * 16;
-          bdst[q] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((pc ^ (r & 7)) << 4));
-          if (r < nj) bstore |= 1u << q;
-          if (pid != 0xffffffffu) bload |= 1u << q;
-        }
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int st = it % stages;
-          if (!pwait(&S.empty[st], ((it / stages) & 1) ^ 1, lim, abort, a.err)) {
-            ok = false;
-            break;
+              for (int b = 0; b < GB / BOX_ROWS; ++b)
+                tma_load_2d(d0 + (uint32_t)b * chunk_box, &xmap, x, (int)s + b * BOX_ROWS, &S.afull[kc]);
+            }
+            const int st = it % stages;
+            if (!pwait(&S.empty[st], ((it / stages) & 1) ^ 1, lim, abort, a.err)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&S.full[st], (uint32_t)nbox * chunk_box);
+            const uint32_t d0 = smem_u32(bring + (size_t)st * a.b_stage_bytes);
+            for (int b = 0; b < nbox; ++b) tma_load_2d(d0 + (uint32_t)b * chunk_box, &xmap, x, y0 + b * BOX_ROWS, &S.full[st]);
           }
-          const uint32_t d0 = smem_u32(bring + (size_t)st * a.b_stage_bytes);
-#pragma unroll
-          for (int q = 0; q < B_PER; ++q)
-            if ((bstore >> q) & 1u) cp_async16(d0 + bdst[q], bsrc[q] + kc * 128, (bload >> q) & 1u);
-          cp_async_arrive(&S.full[st]);
+          if (useA) ++auses;
         }
       }
     }
-    cp_async_commit();  // no copy of this thread may be in flight at exit
-    cp_async_wait<0>();
+    __syncwarp();
   } else if (warp == PW) {
     // ---------------- prep warp: per unit, the (norm, scale, id) of its
     // columns and (first unit) of the tile's own rows into a slot, ahead of
-    // the loaders; per tile whose band needs several units, the own rows into
-    // the resident A region, chunk kc as soon as the previous tile's last MMA
-    // reading that chunk has completed
-    uint32_t u = 0, auses = 0;
+    // the MMA and the epilogue (contiguous reads: the tree's order)
+    uint32_t u = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TileGeom g = tile_geom(a, t);
@@ -483,9 +496,8 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
           ok = false;
           break;
         }
-        Ent* se = slots + sl * SLOT_ENTS;
-        // rows outside the matrix get a NaN norm: they never pass a screen
-        uint32_t ids[SLOT_ENTS / 32];
+        const SlotView se = slot_view<F8>(slots, sl);
+        // rows outside the matrix get an infinite norm: they never pass a screen
 #pragma unroll
         for (int m = 0; m < SLOT_ENTS / 32; ++m) {
           const int e = lane + 32 * m;
@@ -498,43 +510,21 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
             pos = s + (e - SLOT_COLS);
             valid = j == 0 && pos < a.n;
           }
-          ids[m] = valid ? __ldg(a.sigma + pos) : 0xffffffffu;
-        }
-#pragma unroll
-        for (int m = 0; m < SLOT_ENTS / 32; ++m) {
-          const float2 mt =
-              ids[m] != 0xffffffffu ? __ldg(a.meta + ids[m]) : make_float2(__uint_as_float(0x7fc00000u), 0.f);
-          Ent en;
-          ent_set(en, mt.x, mt.y, ids[m]);
-          se[lane + 32 * m] = en;
+          const uint32_t id = valid ? __ldg(a.sigma + pos) : 0xffffffffu;
+          const float2 mt = valid ? __ldg(a.ms + pos) : make_float2(INFINITY, 0.f);
+          se.nrm[e] = mt.x;
+          if (F8) se.sc[e] = mt.y;
+          se.id[e] = id;
+          // the own rows' lists into L2: the epilogue reads them when it
+          // starts the tile, a few units from now
+          if (e >= SLOT_COLS && valid) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.ldist + (size_t)id * KP));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.lidx + (size_t)id * KP));
+          }
         }
         mbar_arrive(&S.mfull[sl]);
-        if (g.J > 1 && j == 0) {
-          __syncwarp();  // the own rows' ids written by the other lanes
-          const uint32_t par = (auses & 1) ^ 1;
-          for (int kc = 0; kc < nk && ok; ++kc) {
-            if (!pwait(&S.aempty[kc], par, lim, abort, a.err)) {
-              ok = false;
-              break;
-            }
-            const uint32_t d0 = smem_u32(aregion + (size_t)kc * GB * 128);
-#pragma unroll 4
-            for (int q = 0; q < A_PER; ++q) {
-              const int e = lane + 32 * q;
-              const int r = e >> 3, pc = e & 7;
-              const uint32_t pid = se[SLOT_COLS + r].id;
-              const uint8_t* src = a.xq + (pid != 0xffffffffu ? (size_t)pid * a.rowb : 0) + kc * 128 + pc * 16;
-              cp_async16(d0 + (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((pc ^ (r & 7)) << 4)), src,
-                         pid != 0xffffffffu);
-            }
-            cp_async_arrive(&S.afull[kc]);
-          }
-          ++auses;
-        }
       }
     }
-    cp_async_commit();
-    cp_async_wait<0>();
   } else if (warp == MW) {
     // ---------------- MMA issuer (one lane)
     if (lane == 0) {
@@ -564,9 +554,6 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
               ok = false;
               break;
             }
-            // the stage was written by cp.async (generic proxy) and is read
-            // by the tensor core (async proxy)
-            fence_proxy_async_smem();
             tc_fence_after();
             const uint32_t chunk = bb + (uint32_t)(st * a.b_stage_bytes);
             const uint32_t achunk = g.J == 1 ? chunk + (uint32_t)(g.W8 >> 3) * 1024u : ab + (uint32_t)kc * GB * 128u;
@@ -589,7 +576,7 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp >= EW0) {
     // ---------------- epilogue: warp EW0 + q + 4 h owns tensor-memory lanes
     // 32 q .. 32 q + 31 (tile rows) and the 32-column chunks of parity h
     const int h = (warp - EW0) >> 2;
@@ -617,12 +604,11 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
           ok = false;
           break;
         }
-        const Ent* se = slots + sl * SLOT_ENTS;
+        const SlotView se = slot_view<F8>(slots, sl);
         if (j == 0) {
-          const Ent own = se[SLOT_COLS + r];
-          ip = own.id;
-          ni = own.nrm;
-          c2 = 2.0f * ent_sc(own);
+          ip = se.id[SLOT_COLS + r];
+          ni = se.nrm[SLOT_COLS + r];
+          c2 = F8 ? 2.0f * se.sc[SLOT_COLS + r] : 2.0f;
           int wr = g.w;
           if (rowok && a.pw) wr = min(wr, (int)__ldg(a.pw + ip));
           // the row's band: columns [r + W8 - wr, r + W8 + wr] except r + W8
@@ -656,24 +642,35 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a) {
           uint32_t wm = 0;
           if (lo <= hi) wm = (0xffffffffu >> (31 - hi + lo)) << lo;
           if (diag >= c0 && diag < c0 + 32) wm &= ~(1u << (diag - c0));
-          // screen against the current last entry (ties pass; the offer
-          // decides); the estimates stay in registers for the hits
-          const float td = L.d[KP - 1];
-          const Ent* ce = se + (c0 - u0);
-          uint32_t hm = 0;
+          // screen: column c passes when its estimate d2 = ni + (n_c - 2 c2' dot)
+          // is at most the list's current last entry (ties pass; the offer
+          // decides); with ti = last - ni (finite even for an unfilled list),
+          // the sign bit of ti - (n_c - ...) marks a miss, and the misses of
+          // the 32 columns are gathered by funnel shifts
+          const float ti = fminf(L.d[KP - 1], 3.0e38f) - ni;
+          const float* cn = se.nrm + (c0 - u0);
+          uint32_t miss = 0;
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj) {
-            const Ent e = ce[jj];
-            const float dot = __uint_as_float(v[jj]);
-            const float d2 = F8 ? fmaf(-c2 * ent_sc(e), dot, ni + e.nrm) : fmaf(-2.0f, dot, ni + e.nrm);
-            v[jj] = __float_as_uint(d2);  // the estimate replaces the dot product
-            hm |= (d2 <= td ? 1u : 0u) << jj;
+          for (int q4 = 0; q4 < 8; ++q4) {
+            const float4 nn = *reinterpret_cast<const float4*>(cn + 4 * q4);
+            float4 ss = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (F8) ss = *reinterpret_cast<const float4*>(se.sc + (c0 - u0) + 4 * q4);
+            const float nv[4] = {nn.x, nn.y, nn.z, nn.w};
+            const float sv[4] = {ss.x, ss.y, ss.z, ss.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int jj = 4 * q4 + e;
+              const float dot = __uint_as_float(v[jj]);
+              const float part = F8 ? fmaf(-c2 * sv[e], dot, nv[e]) : fmaf(-2.0f, dot, nv[e]);
+              v[jj] = __float_as_uint(part);  // the partial estimate replaces the dot product
+              miss = __funnelshift_l(__float_as_uint(ti - part), miss, 1);
+            }
           }
-          hm &= wm;
+          uint32_t hm = __brev(~miss) & wm;
           while (hm) {
             const int jj = __ffs(hm) - 1;
             hm &= hm - 1;
-            L.offer(__uint_as_float(pick32(v, jj)), ce[jj].id);
+            L.offer(__uint_as_float(pick32(v, jj)) + ni, se.id[(c0 - u0) + jj]);
           }
         }
         tc_fence_before();
@@ -867,11 +864,10 @@ GramPlan gram_plan(int d, int wmax, bool f8, int smem_cap) {
   const int W8 = (wmax + 7) & ~7;
   const int ncol = GB + 2 * W8;
   const int J = (ncol + SLOT_COLS - 1) / SLOT_COLS;
-  const int stage_rows = J == 1 ? ncol : SLOT_COLS;
-  p.b_stage_bytes = (uint32_t)stage_rows * 128u;
+  const int stage_rows = (J == 1 ? ncol : SLOT_COLS) + BOX_ROWS - 1;  // whole boxes
+  p.b_stage_bytes = (uint32_t)(stage_rows / BOX_ROWS * BOX_ROWS) * 128u;
   const size_t a_bytes = J > 1 ? (size_t)p.nk * GB * 128 : 0;
-  const size_t ent = f8 ? 16 : 8;
-  const size_t slot_bytes = (size_t)NSLOT * SLOT_ENTS * ent;
+  const size_t slot_bytes = (size_t)NSLOT * SLOT_ENTS * (f8 ? 12 : 8);
   const size_t x_bytes = (size_t)2 * XE * GB * 4;
   const size_t bar_bytes = (sizeof(Bars) + 127) / 128 * 128;
   size_t off = 0;
@@ -884,7 +880,7 @@ GramPlan gram_plan(int d, int wmax, bool f8, int smem_cap) {
   if (st > MAX_STAGES) st = MAX_STAGES;
   if (st < 2) return p;
   p.stages = st;
-  off += (size_t)st * p.b_stage_bytes;
+  off += (size_t)st * p.b_stage_bytes;  // stage sizes are multiples of 4 KB
   p.slot_off = (uint32_t)off;
   off += slot_bytes;
   p.x_off = (uint32_t)off;
@@ -899,8 +895,40 @@ GramPlan gram_plan(int d, int wmax, bool f8, int smem_cap) {
   return p;
 }
 
+// Tensor map of the position-ordered operand rows xs [n][rowb bytes]: boxes
+// of 128 bytes x 32 rows, 128-byte swizzle (the layout the MMA descriptors
+// read), zero fill outside the matrix.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_row_map(CUtensorMap* map, const void* xs, int64_t n, int rowb, bool f8) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return HF_ECUDA;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  const int esz = f8 ? 1 : 2;
+  const cuuint64_t gdim[2] = {(cuuint64_t)(rowb / esz), (cuuint64_t)n};
+  const cuuint64_t gstride[1] = {(cuuint64_t)rowb};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)BOX_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(xs), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? HF_OK : HF_ECUDA;
+}
+
 template <int KP, bool F8>
-int launch_band(const GramArgs& a, size_t smem, cudaStream_t s) {
+int launch_band(const GramArgs& a, const CUtensorMap& map, size_t smem, cudaStream_t s) {
   if (cudaFuncSetAttribute((const void*)gram_band_kernel<KP, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
@@ -909,7 +937,7 @@ int launch_band(const GramArgs& a, size_t smem, cudaStream_t s) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (a.n + GB - 1) / GB;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  gram_band_kernel<KP, F8><<<grid, PT, smem, s>>>(a);
+  gram_band_kernel<KP, F8><<<grid, PT, smem, s>>>(a, map);
   hf_after_launch(F8 ? "gram_band_kernel<fp8>" : "gram_band_kernel<bf16>", s);
   return HF_OK;
 }
@@ -935,21 +963,31 @@ void launch_prepare_operands(const float* x, int64_t n, int d, int form, void* x
   }
 }
 
-int launch_gram_window(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma, int w,
-                       const int32_t* tile_w, const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err,
+void launch_gather_rows(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma,
+                        void* xs, float2* ms, cudaStream_t s) {
+  const int rowb = (int)gram_row_bytes(d, form);
+  gather_rows_kernel<<<hf_blocks(n * (rowb / 16), 256, 152 * 32), 256, 0, s>>>(
+      static_cast<const uint8_t*>(xq), meta, sigma, n, rowb, static_cast<uint8_t*>(xs), ms);
+  hf_after_launch("gather_rows_kernel", s);
+}
+
+int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w, const int32_t* tile_w,
+                       const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err, const void* xs, const float2* ms,
                        cudaStream_t s) {
   const bool f8 = form == 2;
   const GramPlan p = gram_plan(d, w, f8, max_smem_optin());
   if (!p.ok) return HF_EINVAL;
+  alignas(64) CUtensorMap map;
+  const int rc = make_row_map(&map, xs, n, p.rowb, f8);
+  if (rc != HF_OK) return rc;
   GramArgs a;
-  a.xq = static_cast<const uint8_t*>(xq);
-  a.meta = meta;
+  a.ms = ms;
   a.sigma = sigma;
   a.tile_w = tile_w;
   a.pw = pw;
   a.n = n;
-  a.rowb = p.rowb;
   a.nk = p.nk;
+  a.elem_per_chunk = f8 ? 128 : 64;
   a.w = w;
   a.stages = p.stages;
   a.a_off = p.a_off;
@@ -963,10 +1001,10 @@ int launch_gram_window(const void* xq, const float2* meta, int form, int64_t n, 
   a.err = err;
   a.spin_limit = 2000000000ull;  // 2 s per wait (globaltimer nanoseconds)
   switch (kp * 2 + (f8 ? 1 : 0)) {
-    case 32: return launch_band<16, false>(a, p.smem, s);
-    case 33: return launch_band<16, true>(a, p.smem, s);
-    case 64: return launch_band<32, false>(a, p.smem, s);
-    case 65: return launch_band<32, true>(a, p.smem, s);
+    case 32: return launch_band<16, false>(a, map, p.smem, s);
+    case 33: return launch_band<16, true>(a, map, p.smem, s);
+    case 64: return launch_band<32, false>(a, map, p.smem, s);
+    case 65: return launch_band<32, true>(a, map, p.smem, s);
     default: return HF_EINVAL;
   }
 }

@@ -132,8 +132,15 @@ size_t gram_row_bytes(int d, int form);  // operand row pitch in bytes
 void launch_prepare_operands(const float* x, int64_t n, int d, int form, void* xq, float2* meta, cudaStream_t s);
 // one tree: tile_w (per tile of 128 positions, this tree's window) and pw
 // (per point window) may be null, then every point uses w
-int launch_gram_window(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma, int w,
-                       const int32_t* tile_w, const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err,
+// one tree's operand rows and (norm, scale) in its position order:
+// xs[p] = xq[sigma[p]] (n x gram_row_bytes), ms[p] = meta[sigma[p]]
+void launch_gather_rows(const void* xq, const float2* meta, int form, int64_t n, int d, const uint32_t* sigma,
+                        void* xs, float2* ms, cudaStream_t s);
+// one tree from its gathered rows; tile_w (per tile of 128 positions, this
+// tree's window; 0 skips the tile) and pw (per point window) may be null,
+// then every point uses w
+int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w, const int32_t* tile_w,
+                       const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err, const void* xs, const float2* ms,
                        cudaStream_t s);
 int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
                   cudaStream_t s);

@@ -53,21 +53,25 @@ struct ListK {
   // Inserts (cd, ci) unless it is no better than the last slot or listed.
   __device__ __forceinline__ void offer(float cd, uint32_t ci) {
     if (!lessp(cd, ci, d[KP - 1], i[KP - 1])) return;
-    // one bit per slot, combined by balanced trees (short dependency chains)
-    uint32_t dupm[KP], lowm[KP];
+    // a listed candidate (the common case once lists have settled: the same
+    // neighbour comes back in later trees) leaves before the insertion work
+    uint32_t dupm[KP];
 #pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      dupm[j] = i[j] == ci ? 1u : 0u;
-      lowm[j] = lessp(d[j], i[j], cd, ci) ? 1u : 0u;
-    }
+    for (int j = 0; j < KP; ++j) dupm[j] = i[j] == ci ? 1u : 0u;
 #pragma unroll
     for (int w = 1; w < KP; w <<= 1)
 #pragma unroll
-      for (int j = 0; j + w < KP; j += 2 * w) {
-        dupm[j] |= dupm[j + w];
-        lowm[j] += lowm[j + w];
-      }
+      for (int j = 0; j + w < KP; j += 2 * w) dupm[j] |= dupm[j + w];
     if (dupm[0]) return;
+    // insert position: the number of entries below the candidate (balanced
+    // tree of bits: short dependency chains)
+    uint32_t lowm[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) lowm[j] = lessp(d[j], i[j], cd, ci) ? 1u : 0u;
+#pragma unroll
+    for (int w = 1; w < KP; w <<= 1)
+#pragma unroll
+      for (int j = 0; j + w < KP; j += 2 * w) lowm[j] += lowm[j + w];
     // entries below the candidate form a prefix; each slot then takes its new
     // value from the old list independently
     const uint32_t below = lowm[0];
