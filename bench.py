@@ -48,8 +48,8 @@ MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 # DRAM traffic of the dominant kernels from one ncu capture of a 1M-point
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
-WINDOW_TRAFFIC = {"bytes_per_point": 1915, "source_sha": "c47a6c4277b03192", "file": "window.cu"}
-GRAM_TRAFFIC = {"bytes_per_point": 1134, "source_sha": "1ba5dabd3b9deee8", "file": "gram.cu"}
+WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "17ad84a8c61fc969", "file": "window.cu"}   # w = 32
+GRAM_TRAFFIC = {"bytes_per_point": 1131, "source_sha": "eb33dfa67f0cefa9", "file": "gram.cu"}     # w = 512
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
@@ -447,7 +447,8 @@ def gram_roofline(a, launch_ms, gather_ms=0.0):
     g_bytes = 2.0 * a.n * rowb + 16.0 * a.n
     out = {"bound": "tensor", "kernel": "gram_band_kernel (A5+A6: tcgen05 Gram band + top-k merge)",
            "achieved": t_ach, "peak": tf_peak, "unit": "TFLOP/s", "frac": t_ach / tf_peak,
-           "traffic": None, "flops_per_launch": flops, "launch_ms": launch_ms,
+           "traffic": traffic_per_launch(GRAM_TRAFFIC, a.n) if a.w == 512 and not fp8 else None,
+           "flops_per_launch": flops, "launch_ms": launch_ms,
            "peak_note": f"bf16_tflops_sustained {src} (MEASURED_PEAKS.json)" + (" x 2 for e4m3" if fp8 else ""),
            "hbm_side": {"achieved": b_ach, "peak": hbm_peak, "unit": "GB/s", "frac": b_ach / hbm_peak,
                         "bytes_per_launch": bytes_launch, "bytes_per_point": per_point}}
@@ -457,8 +458,7 @@ def gram_roofline(a, launch_ms, gather_ms=0.0):
                          "frac": ga / hbm_peak, "bytes": g_bytes}
     if t_ach / tf_peak < b_ach / hbm_peak:  # narrow windows: the HBM side dominates
         out.update({"bound": "hbm", "achieved": b_ach, "peak": hbm_peak, "unit": "GB/s", "frac": b_ach / hbm_peak,
-                    "peak_note": f"hbm_gbs {src} (MEASURED_PEAKS.json)",
-                    "traffic": traffic_per_launch(GRAM_TRAFFIC, a.n)})
+                    "peak_note": f"hbm_gbs {src} (MEASURED_PEAKS.json)"})
     return out
 
 
@@ -471,7 +471,7 @@ def window_roofline(a, launch_ms):
     peak = SMS * FP32_LANES * MAX_SM_MHZ * 1e6 * 1.5 / 1e12
     return {"bound": "alu", "kernel": "window_kernel (A5+A6, plain f32)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic_per_launch(WINDOW_TRAFFIC, n), "launch_ms": launch_ms,
+            "traffic": traffic_per_launch(WINDOW_TRAFFIC, n) if w == 32 else None, "launch_ms": launch_ms,
             "peak_note": "152 SMs x 128 FP32 lanes x 2070 MHz, 3 flops per FADD+FFMA pair"}
 
 

@@ -173,6 +173,89 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
 int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
                      int32_t* out_idx, float* out_dist, void* stream);
 
+/* ---- learned per-point budget ---------------------------------------------
+ * The paper spends one budget -- the number of sorts T and the window k1
+ * around each position (Algorithm 2; Table 2 trades recall against it) -- on
+ * every point. These calls learn a budget per point from its coordinates and
+ * apply it. They are an extension of the method, not part of the paper.
+ */
+
+/*
+ * hf_budget_labels -- training targets from a built forest: for each point i,
+ * the cheapest cell (T, w) of the grid t_grid x w_grid (cost T * (128 + 2 w))
+ * at which at least min_hits of its exact neighbours knn[i][0..k) lie within
+ * w positions of i in one of the first T orders (Algorithm 2's candidate
+ * rule); the largest cell when none does.
+ * knn         : device, n x k int32 exact neighbours of every point (-1 =
+ *               none), e.g. from hf_knn_graph with w >= n - 1 (every pair);
+ * t_grid      : host, nt ascending tree counts in [1, forest T], nt <= 16;
+ * w_grid      : host, nw ascending windows >= 1, nw <= 16;
+ * out_targets : device, n x 2 float: (log2 w, log2 T) of the cell;
+ * out_cell    : device, n int32: cell index a * nw + b (t_grid[a], w_grid[b]).
+ */
+int hf_budget_labels(hf_forest* f, const int32_t* knn, int32_t k, const int32_t* t_grid, int32_t nt,
+                     const int32_t* w_grid, int32_t nw, int32_t min_hits, float* out_targets, int32_t* out_cell,
+                     void* stream);
+
+/*
+ * hf_knn_graph_budget -- hf_knn_graph with a budget per point: point i takes
+ * part in trees t < T_pt[i] with window w_pt[i] (its candidates are the
+ * points within w_pt[i] positions of it in those orders; 0 trees or a 0
+ * window leave it out); the band kernel works on each 128-position tile up
+ * to the tile's largest window and skips tiles with none. Tensor forms only
+ * (hf_set_option mode 1 or 2; HF_ENOTIMPL otherwise).
+ * w_pt, T_pt : device, n int32 each;
+ * w_max      : the largest w_pt (1 .. 65535; larger entries are cut to it);
+ * T_max      : the largest T_pt (1 .. forest T; trees past it are not used).
+ * Outputs as hf_knn_graph.
+ */
+int hf_knn_graph_budget(hf_forest* f, int32_t k, const int32_t* w_pt, const int32_t* T_pt, int32_t w_max,
+                        int32_t T_max, int32_t* out_idx, float* out_dist, void* stream);
+
+/*
+ * The budget model: an MLP d -> 256 -> 256 -> 2 with GELU activations
+ * (GELU(z) = z Phi(z)), predicting (log2 w, log2 T). Weights, inputs and
+ * activations are stored in BF16, every product is accumulated in FP32 on the
+ * tensor cores (tcgen05); the fp32 master weights are updated by Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8). The loss of a batch of B rows is
+ * L = 1/(2B) sum over rows and both outputs of (y - target)^2.
+ * Parameters in packed order (floats): W1 [256][d], b1 [256], W2 [256][256],
+ * b2 [256], W3 [2][256], b3 [2]; layer l computes z = W h + b.
+ */
+typedef struct hf_mlp hf_mlp; /* opaque; owned by the library */
+
+/* hf_mlp_create -- a model for d inputs on the current device, weights
+ * uniform in +-1/sqrt(fan_in) from splitmix64(seed), biases 0. */
+int hf_mlp_create(int32_t d, uint64_t seed, hf_mlp** out);
+/* hf_mlp_free -- releases the model (NULL is a no-op). */
+int hf_mlp_free(hf_mlp* m);
+/* hf_mlp_param_count -- number of floats in the packed parameter order. */
+int hf_mlp_param_count(const hf_mlp* m, int64_t* out);
+/* hf_mlp_get_params / hf_mlp_set_params -- the fp32 master weights in packed
+ * order (host floats); set_params also refreshes the BF16 copies. */
+int hf_mlp_get_params(const hf_mlp* m, float* out);
+int hf_mlp_set_params(hf_mlp* m, const float* params);
+/*
+ * hf_mlp_predict -- outputs of n rows: x device n x d float32, out n x 2
+ * float32 (device or host).
+ */
+int hf_mlp_predict(hf_mlp* m, const float* x, int64_t n, float* out, void* stream);
+/*
+ * hf_mlp_grads -- loss and gradients (packed order, host floats) of one batch
+ * of B rows (128 <= B <= 8192, a multiple of 128): x device B x d, targets
+ * B x 2 (device or host). Weights unchanged.
+ */
+int hf_mlp_grads(hf_mlp* m, const float* x, const float* targets, int32_t B, float* out_grads, float* out_loss,
+                 void* stream);
+/*
+ * hf_mlp_train -- `steps` Adam steps with learning rate lr on consecutive
+ * batches of B rows (wrapping around) of the device-resident training set
+ * x (n x d) and targets (n x 2); *out_loss gets the mean batch loss of the
+ * last min(steps, 50) steps.
+ */
+int hf_mlp_train(hf_mlp* m, const float* x, const float* targets, int64_t n, int32_t B, int32_t steps, float lr,
+                 float* out_loss, void* stream);
+
 /* hf_free -- releases the forest and everything it owns (NULL is a no-op). */
 int hf_free(hf_forest* f);
 

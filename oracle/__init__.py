@@ -18,3 +18,4 @@ from .hilbert_forest import (  # noqa: F401
     permute_reflect, quantize, query_codes, recall, search, skilling_transpose,
     sq_dist_fp64, topk_from_candidates, tree_params, window_candidates,
 )
+from . import budget  # noqa: F401,E402  (learned per-point budget: labels, MLP, budgeted graph)

@@ -31,6 +31,8 @@ SYMBOLS = [
     "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
     "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
     "hf_launch_count", "hf_search_static", "hf_trim_pool",
+    "hf_budget_labels", "hf_knn_graph_budget", "hf_mlp_create", "hf_mlp_free", "hf_mlp_param_count",
+    "hf_mlp_get_params", "hf_mlp_set_params", "hf_mlp_predict", "hf_mlp_grads", "hf_mlp_train",
 ]
 
 _lib = None
@@ -71,6 +73,16 @@ def lib() -> ctypes.CDLL:
         "hf_launch_count": [],
         "hf_search_static": [vp, vp, i64, i32, i32, vp, vp, vp],
         "hf_trim_pool": [],
+        "hf_budget_labels": [vp, vp, i32, vp, i32, vp, i32, i32, vp, vp, vp],
+        "hf_knn_graph_budget": [vp, i32, vp, vp, i32, i32, vp, vp, vp],
+        "hf_mlp_create": [i32, u64, pp],
+        "hf_mlp_free": [vp],
+        "hf_mlp_param_count": [vp, vp],
+        "hf_mlp_get_params": [vp, vp],
+        "hf_mlp_set_params": [vp, vp],
+        "hf_mlp_predict": [vp, vp, i64, vp, vp],
+        "hf_mlp_grads": [vp, vp, vp, i32, vp, vp, vp],
+        "hf_mlp_train": [vp, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -229,6 +241,40 @@ class Forest:
                "hf_search_static")
         return out_idx, out_dist
 
+    def knn_graph_budget(self, k: int, w_pt, T_pt, out_idx=None, out_dist=None):
+        """hf_knn_graph_budget: point i takes part in trees t < T_pt[i] with
+        window w_pt[i] (CUDA int32 tensors of n entries); tensor forms only."""
+        if out_idx is None:
+            out_idx = _empty_like_input(self._points, (self.n, k), "int32")
+        if out_dist is None:
+            out_dist = _empty_like_input(self._points, (self.n, k), "float32")
+        wmax, tmax = int(w_pt.max().item()), int(T_pt.max().item())
+        wp, _w = _ptr(w_pt)
+        tp, _t = _ptr(T_pt)
+        ip, _a = _ptr(out_idx)
+        dp, _b = _ptr(out_dist)
+        _check(lib().hf_knn_graph_budget(self._h, k, wp, tp, max(1, wmax), max(1, tmax), ip, dp,
+                                         _stream(out_idx, out_dist, w_pt)), "hf_knn_graph_budget")
+        return out_idx, out_dist
+
+    def budget_labels(self, knn, t_grid, w_grid, min_hits: int, out_targets=None, out_cell=None):
+        """hf_budget_labels: (targets float32[n, 2] = (log2 w, log2 T), cell
+        int32[n]) from the exact neighbours knn (CUDA int32 [n, k])."""
+        import torch
+        n, k = knn.shape
+        if out_targets is None:
+            out_targets = torch.empty((n, 2), dtype=torch.float32, device=knn.device)
+        if out_cell is None:
+            out_cell = torch.empty(n, dtype=torch.int32, device=knn.device)
+        tg = np.ascontiguousarray(t_grid, dtype=np.int32)
+        wg = np.ascontiguousarray(w_grid, dtype=np.int32)
+        kp, _k = _ptr(knn)
+        op, _o = _ptr(out_targets)
+        cp, _c = _ptr(out_cell)
+        _check(lib().hf_budget_labels(self._h, kp, k, tg.ctypes.data, len(tg), wg.ctypes.data, len(wg), min_hits,
+                                      op, cp, _stream(knn)), "hf_budget_labels")
+        return out_targets, out_cell
+
     def set_option(self, key: str, value: int):
         _check(lib().hf_set_option(self._h, key.encode(), value), "hf_set_option")
 
@@ -271,3 +317,66 @@ class Forest:
 
 def build(points, T: int, bits: int = 8, seed: int = 3, options: str | None = None) -> Forest:
     return Forest(points, T, bits, seed, options)
+
+
+class Mlp:
+    """The budget model (hf_mlp_*): d -> 256 -> 256 -> 2, GELU, BF16 weights
+    and activations, FP32 accumulation on the tensor cores, Adam."""
+
+    def __init__(self, d: int, seed: int = 5):
+        h = ctypes.c_void_p()
+        _check(lib().hf_mlp_create(d, seed, ctypes.byref(h)), "hf_mlp_create")
+        self._h, self.d = h, int(d)
+        cnt = ctypes.c_int64()
+        lib().hf_mlp_param_count(self._h, ctypes.byref(cnt))
+        self.nparam = int(cnt.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hf_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.nparam, np.float32)
+        _check(lib().hf_mlp_get_params(self._h, out.ctypes.data), "hf_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().hf_mlp_set_params(self._h, p.ctypes.data), "hf_mlp_set_params")
+
+    def predict(self, x, out=None):
+        """x: CUDA float32 [n, d] -> [n, 2]."""
+        n = x.shape[0]
+        if out is None:
+            out = _empty_like_input(x, (n, 2), "float32")
+        xp, _x = _ptr(x)
+        op, _o = _ptr(out)
+        _check(lib().hf_mlp_predict(self._h, xp, n, op, _stream(x, out)), "hf_mlp_predict")
+        return out
+
+    def grads(self, x, targets):
+        """(loss, packed gradients) of one batch (CUDA x [B, d], targets [B, 2])."""
+        B = x.shape[0]
+        g = np.empty(self.nparam, np.float32)
+        loss = np.zeros(1, np.float32)
+        xp, _x = _ptr(x)
+        tp, _t = _ptr(targets)
+        _check(lib().hf_mlp_grads(self._h, xp, tp, B, g.ctypes.data, loss.ctypes.data, _stream(x, targets)),
+               "hf_mlp_grads")
+        return float(loss[0]), g
+
+    def train(self, x, targets, batch: int, steps: int, lr: float):
+        """Adam steps on the CUDA training set; the mean loss of the last steps."""
+        loss = np.zeros(1, np.float32)
+        xp, _x = _ptr(x)
+        tp, _t = _ptr(targets)
+        _check(lib().hf_mlp_train(self._h, xp, tp, x.shape[0], batch, steps, lr, loss.ctypes.data,
+                                  _stream(x, targets)), "hf_mlp_train")
+        return float(loss[0])

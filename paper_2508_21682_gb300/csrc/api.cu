@@ -499,11 +499,18 @@ int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
   return HF_OK;
 }
 
-int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
-  if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// The graph over the first T_use trees. wpt / tpt (device, per point; both or
+// neither): point i takes part in tree t < tpt[i] with window wpt[i] (w is
+// then the largest window); the tensor forms only.
+int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const int32_t* tpt, int T_use,
+                   int32_t* out_idx, float* out_dist, cudaStream_t s) {
   cudaGetLastError();  // an earlier call's error was reported by that call
   const int64_t n = f->n;
+  const bool budget = wpt != nullptr;
   // Plain mode: the window kernel keeps the top kp >= k per point by exact
   // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= k + 1
   // (by default) by the BF16 expansion, then the re-rank orders them by exact
@@ -511,6 +518,7 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   const int form = f->mode >= 1 && gram_supported(f->d, w, f->mode) ? f->mode : 0;
   const bool tensor = form != 0;
   if (!tensor && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;  // widest window the plain band launches cover
+  if (!tensor && budget) return HF_ENOTIMPL;              // per-point windows: tensor forms only
   f->timings[8] = (float)form;  // the form that runs
   const int slack = f->tensor_slack < 0 ? 1 : f->tensor_slack;
   const int kp = window_list_pitch(tensor ? k + slack : k);
@@ -519,8 +527,12 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   float* ldd = nullptr;
   void* xs = nullptr;  // tensor forms: one tree's rows in its order
   float2* ms = nullptr;
+  uint16_t* pw = nullptr;     // per-point windows of one tree
+  int32_t* tile_w = nullptr;  // per-tile windows of one tree
   cudaError_t e = dalloc(&li, (size_t)n * kp, s);
   if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp, s);
+  if (e == cudaSuccess && budget) e = dalloc(&pw, (size_t)n, s);
+  if (e == cudaSuccess && budget) e = dalloc(&tile_w, (size_t)(n + 127) / 128, s);
   if (e == cudaSuccess && tensor) e = dalloc_bytes(&xs, (size_t)n * gram_row_bytes(f->d, form), s);
   if (e == cudaSuccess && tensor) e = dalloc(&ms, (size_t)n, s);
   if (e == cudaSuccess && tensor && f->xform != form) {
@@ -539,20 +551,23 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
     dfree(ldd, s);
     dfree(xs, s);
     dfree(ms, s);
+    dfree(pw, s);
+    dfree(tile_w, s);
     return map_cuda(e);
   }
   Timer tm(f, s);
   cudaEvent_t a0 = tm.mark();
   launch_list_init(li, ldd, n * kp, s);
   int rc = HF_OK;
-  for (int t = 0; t < f->T && rc == HF_OK; ++t) {
+  for (int t = 0; t < T_use && rc == HF_OK; ++t) {
     if (tensor) {
+      const uint32_t* sig = f->sigma + (size_t)t * n;
+      if (budget) launch_tree_budget(sig, n, t, wpt, tpt, pw, tile_w, s);
       cudaEvent_t g0 = tm.mark();
-      launch_gather_rows(f->xb, f->xmeta, form, n, f->d, f->sigma + (size_t)t * n, xs, ms, s);
+      launch_gather_rows(f->xb, f->xmeta, form, n, f->d, sig, xs, ms, s);
       cudaEvent_t g1 = tm.mark();
       tm.span(9, g0, g1);
-      rc = launch_gram_window(form, n, f->d, f->sigma + (size_t)t * n, w, nullptr, nullptr, kp, li, ldd, f->err, xs,
-                              ms, s);
+      rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs, ms, s);
     } else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }
@@ -587,7 +602,60 @@ int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* ou
   dfree(ldd, s);
   dfree(xs, s);
   dfree(ms, s);
+  dfree(pw, s);
+  dfree(tile_w, s);
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hf_knn_graph(hf_forest* f, int32_t k, int32_t w, int32_t* out_idx, float* out_dist, void* stream) {
+  if (!f || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  return knn_graph_impl(f, k, w, nullptr, nullptr, f->T, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+int hf_knn_graph_budget(hf_forest* f, int32_t k, const int32_t* w_pt, const int32_t* T_pt, int32_t w_max,
+                        int32_t T_max, int32_t* out_idx, float* out_dist, void* stream) {
+  if (!f || !w_pt || !T_pt || !out_idx || !out_dist || k < 1 || k > HF_MAX_K || w_max < 1 || w_max > 65535 ||
+      T_max < 1 || T_max > f->T)
+    return HF_EINVAL;
+  if (classify(w_pt) != 1 || classify(T_pt) != 1) return HF_EINVAL;
+  return knn_graph_impl(f, k, w_max, w_pt, T_pt, T_max, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+int hf_budget_labels(hf_forest* f, const int32_t* knn, int32_t k, const int32_t* t_grid, int32_t nt,
+                     const int32_t* w_grid, int32_t nw, int32_t min_hits, float* out_targets, int32_t* out_cell,
+                     void* stream) {
+  if (!f || !knn || !t_grid || !w_grid || !out_targets || !out_cell || k < 1 || k > HF_MAX_K || nt < 1 || nw < 1 ||
+      nt > 16 || nw > 16 || min_hits < 0 || min_hits > k)
+    return HF_EINVAL;
+  if (classify(knn) != 1 || classify(out_targets) != 1 || classify(out_cell) != 1) return HF_EINVAL;
+  int tmax = 0;
+  for (int i = 0; i < nt; ++i) {
+    if (t_grid[i] < 1 || t_grid[i] > f->T || (i && t_grid[i] <= t_grid[i - 1])) return HF_EINVAL;
+    tmax = t_grid[i];
+  }
+  for (int i = 0; i < nw; ++i)
+    if (w_grid[i] < 1 || (i && w_grid[i] <= w_grid[i - 1])) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  int32_t *pos = nullptr, *tg = nullptr, *wg = nullptr;
+  cudaError_t e = dalloc(&pos, (size_t)tmax * f->n, s);
+  if (e == cudaSuccess) e = dalloc(&tg, (size_t)nt, s);
+  if (e == cudaSuccess) e = dalloc(&wg, (size_t)nw, s);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) {
+    cudaMemcpyAsync(tg, t_grid, (size_t)nt * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(wg, w_grid, (size_t)nw * 4, cudaMemcpyHostToDevice, s);
+    rc = launch_budget_labels(f->sigma, tmax, f->n, knn, k, tg, nt, wg, nw, min_hits, out_targets, out_cell, pos, s);
+  }
+  const int rc2 = finish(f, s);
+  dfree(pos, s);
+  dfree(tg, s);
+  dfree(wg, s);
+  return rc != HF_OK ? rc : rc2;
 }
 
 int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w, int32_t* out_idx,

@@ -145,6 +145,16 @@ int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w,
 int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
                   cudaStream_t s);
 
+// budget.cu
+// labels from the inverse orders of the first T trees (pos: T x n scratch)
+int launch_budget_labels(const uint32_t* sigma, int T, int64_t n, const int32_t* knn, int k, const int32_t* tg,
+                         int ntg, const int32_t* wg, int nwg, int min_hits, float* out, int32_t* cell, int32_t* pos,
+                         cudaStream_t s);
+// tree t's per-point windows pw (0: the point sits this tree out) and per-tile
+// largest windows tile_w from per-point (w, T) budgets
+void launch_tree_budget(const uint32_t* sigma, int64_t n, int t, const int32_t* wpt, const int32_t* tpt, uint16_t* pw,
+                        int32_t* tile_w, cudaStream_t s);
+
 // search.cu
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,
                   int w, uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree,
