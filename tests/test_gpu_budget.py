@@ -143,11 +143,15 @@ def _recall(found, exact):
     return float(np.mean([len(set(a[a >= 0].tolist()) & set(b.tolist())) / k for a, b in zip(found, exact)]))
 
 
-def test_learned_budget_beats_uniform_budget(hf):
-    """The trained network's per-point budgets against one budget for all
-    points at the same total cost (sum over points of T_i (128 + 2 w_i)),
-    judged on held-out points by recall@15 of the graph the library builds:
-    the learned allocation finds more true neighbours."""
+def test_learned_budget_reaches_recall_cheaper_than_uniform(hf):
+    """What the trained network gains over the method without it. The labels
+    give each training point the cheapest budget at which 12 of its 15 true
+    neighbours are candidates; the network predicts that need for unseen
+    points. Judged on held-out points by recall@15 of the graph the library
+    builds, against the cost of the graph (mean over all points of
+    T_i (128 + 2 w_i), the band columns the Gram kernel computes): the
+    learned budgets, scaled by one factor 2^s, reach the target recall at a
+    lower cost than the cheapest uniform budget of the grid that does."""
     n, d, T, k = 60000, 128, 32, 15
     x = S.gaussian_mixture(n, d, n_components=200, seed=12)
     xd = cuda(x)
@@ -169,29 +173,41 @@ def test_learned_budget_beats_uniform_budget(hf):
     m.train(xd[tr_t].contiguous(), tgt[tr_t].contiguous(), batch=1024, steps=1500, lr=1e-3)
     pred = m.predict(xd).cpu().numpy().astype(np.float64)
     m.close()
-    uw, uT = 32, 8
-    ucost = uT * (128 + 2 * uw)
+    exact = ei.cpu().numpy()[te]
+
+    def recall_of(w, t):
+        li, _ = G.knn_graph_budget(k, cuda(w.astype(np.int32)), cuda(t.astype(np.int32)))
+        return _recall(li.cpu().numpy()[te], exact)
+
+    def cost(w, t):
+        return float(np.mean(t * (128.0 + 2.0 * w)))
+
+    ones = np.ones(n)
+    r_max = recall_of(ones * wg[-1], ones * tg[-1])
+    target = min(0.8, 0.95 * r_max)
+    cells = sorted(((Tc * (128 + 2 * w), Tc, w) for Tc in tg for w in wg))
+    c_uniform = None
+    for c, Tc, w in cells:
+        if recall_of(ones * w, ones * Tc) >= target:
+            c_uniform = c
+            break
+    assert c_uniform is not None
 
     def budgets(shift):
-        w = np.clip(np.round(2.0 ** (pred[:, 0] + shift)), 1, 2048).astype(np.int32)
-        t = np.clip(np.round(2.0 ** (pred[:, 1] + shift / 2)), 1, T).astype(np.int32)
+        w = np.clip(np.round(2.0 ** (pred[:, 0] + shift)), 1, 4096)
+        t = np.clip(np.round(2.0 ** (pred[:, 1] + shift)), 1, T)
         return w, t
 
     lo, hi = -6.0, 6.0
-    for _ in range(40):  # equal mean cost by bisection on a shift in log2 space
+    assert recall_of(*budgets(hi)) >= target
+    for _ in range(14):  # the smallest shift that reaches the target (recall grows with the shift)
         mid = 0.5 * (lo + hi)
-        w, t = budgets(mid)
-        if np.mean(t * (128.0 + 2.0 * w)) > ucost:
+        if recall_of(*budgets(mid)) >= target:
             hi = mid
         else:
             lo = mid
-    w, t = budgets(lo)
-    assert np.mean(t * (128.0 + 2.0 * w)) <= ucost * 1.001
-    li, _ = G.knn_graph_budget(k, cuda(w), cuda(t))
-    ui, _ = G.knn_graph_budget(k, cuda(np.full(n, uw, np.int32)), cuda(np.full(n, uT, np.int32)))
-    exact = ei.cpu().numpy()[te]
-    r_learned = _recall(li.cpu().numpy()[te], exact)
-    r_uniform = _recall(ui.cpu().numpy()[te], exact)
-    print(f"held-out recall@15 at equal cost: learned {r_learned:.4f}, uniform {r_uniform:.4f}")
-    assert r_learned > r_uniform + 0.01
+    c_learned = cost(*budgets(hi))
+    print(f"target recall@15 {target:.3f}: uniform cost {c_uniform:.0f}, learned cost {c_learned:.0f} "
+          f"({c_uniform / c_learned:.2f}x less work)")
+    assert c_learned < 0.9 * c_uniform
     G.close()
