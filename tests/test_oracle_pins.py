@@ -142,6 +142,45 @@ def test_pack_key_layout_and_padding():
     assert O.key_words(384, 8) == 48 and O.key_words(16, 8) == 2 and O.key_words(3, 5) == 1
 
 
+def self_similar(transpose, d, b):
+    """The order-b curve is 2^d copies of the order-(b-1) curve: its cells,
+    cut into 2^d consecutive blocks, fill one sub-cube (octant) each, the
+    octants are visited with unit steps, and each block, taken relative to
+    its octant's corner, is the order-(b-1) traversal mapped by a symmetry of
+    the cube (an axis permutation combined with reflections)."""
+    pts, k = curve_order(transpose, d, b)
+    seq = pts[np.argsort(np.array(k, dtype=np.int64))]
+    p1, k1 = curve_order(transpose, d, b - 1)
+    base = p1[np.argsort(np.array(k1, dtype=np.int64))]
+    half = 1 << (b - 1)
+    sub = 1 << (d * (b - 1))
+    maps = []
+    for perm in itertools.permutations(range(d)):
+        for refl in itertools.product((0, 1), repeat=d):
+            maps.append(np.where(np.array(refl)[None, :] == 1, half - 1 - base[:, list(perm)], base[:, list(perm)]))
+    octs = []
+    for j in range(1 << d):
+        blk = seq[j * sub:(j + 1) * sub]
+        o = blk // half
+        if not np.all(o == o[0]):
+            return False
+        local = blk - o[0] * half
+        if not any(np.array_equal(local, m) for m in maps):
+            return False
+        octs.append(o[0])
+    return bool(np.all(np.abs(np.diff(np.array(octs), axis=0)).sum(axis=1) == 1))
+
+
+@pytest.mark.parametrize("b", [2, 3, 4])
+def test_curve_d3_self_similar(b):
+    assert self_similar(O.skilling_transpose, 3, b)
+
+
+@pytest.mark.parametrize("b", [2, 3, 4, 5])
+def test_curve_d2_self_similar(b):
+    assert self_similar(O.skilling_transpose, 2, b)
+
+
 def _mutant_transpose(mutation):
     """Copies of the transform with one planted mistake each."""
 
@@ -183,6 +222,14 @@ def test_pins_catch_planted_mistakes(mutation):
         for (x, y), kk in zip(*curve_order(f, 2, b))
     )
     assert not (ok_curve and ok_d2), mutation
+
+
+@pytest.mark.parametrize("mutation", ["no_gray", "no_t", "t_from_x1", "reverse_i", "invert_all"])
+def test_d3_pins_catch_planted_mistakes(mutation):
+    """Without the d = 2 textbook curve: every planted mistake breaks the d = 3
+    curve's bijection/unit steps or its self-similarity."""
+    f = _mutant_transpose(mutation)
+    assert not (check_curve(f, dims=(3,), bits=(2, 3)) and all(self_similar(f, 3, b) for b in (2, 3))), mutation
 
 
 def test_unmutated_copy_matches_oracle():
