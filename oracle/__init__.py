@@ -19,3 +19,4 @@ from .hilbert_forest import (  # noqa: F401
     sq_dist_fp64, topk_from_candidates, tree_params, window_candidates,
 )
 from . import budget  # noqa: F401,E402  (learned per-point budget: labels, MLP, budgeted graph)
+from . import sketch  # noqa: F401,E402  (second stage: sign sketches, Hamming top-k2)

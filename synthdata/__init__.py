@@ -13,6 +13,13 @@ The generators below stand in for them with the same shapes:
   (means N(0, I), per-axis std U(0.1, 0.5)), rows normalised to unit length.
 * ``mixture_queries`` -- draws from the same mixture plus N(0, noise^2) per
   coordinate, renormalised.
+* ``sketch_projection`` -- the projection matrix of the sign sketches: i.i.d.
+  N(0, 1) entries, one row per sketch bit (the random numbers the sketch
+  stage draws, passed to both sides as an input).
+* ``small_integer_points`` / ``small_integer_projection`` -- integer-valued
+  rows (|v| <= 8) and projections (|v| <= 2): every inner product, squared
+  distance and BF16 rounding of them is exact in float32, so float decisions
+  (sketch signs, distance ties) come out the same on every side.
 
 Every stream is keyed by (seed, stream id, block id) through numpy's Philox
 counter-based bit generator, so a row's values do not depend on how many
@@ -31,16 +38,21 @@ __all__ = [
     "gaussian_mixture",
     "mixture_params",
     "mixture_queries",
+    "sketch_projection",
+    "small_integer_points",
+    "small_integer_projection",
     "SEED_DATA",
     "SEED_QUERIES",
     "SEED_FOREST",
     "SEED_SAMPLE",
+    "SEED_SKETCH",
 ]
 
 SEED_DATA = 1
 SEED_QUERIES = 2
 SEED_FOREST = 3
 SEED_SAMPLE = 4
+SEED_SKETCH = 5
 
 _BLOCK_ROWS = 65536
 
@@ -50,6 +62,8 @@ _S_MEANS = 1
 _S_SIGMAS = 2
 _S_ASSIGN = 3
 _S_NOISE = 4
+_S_PROJ = 5
+_S_INT = 6
 
 
 def _gen(seed: int, stream: int, block: int) -> np.random.Generator:
@@ -135,3 +149,25 @@ def mixture_queries(nq: int, d: int, n_components: int = 1000, data_seed: int = 
     """nq x d float32 queries: the data mixture (parameters from ``data_seed``)
     plus N(0, noise^2) per coordinate, renormalised."""
     return _mixture_rows(nq, d, mixture_params(d, n_components, data_seed), seed, noise)
+
+
+def sketch_projection(bits: int, d: int, seed: int = SEED_SKETCH) -> np.ndarray:
+    """float32 [bits][d], i.i.d. N(0, 1)."""
+    return _gen(seed, _S_PROJ, 0).standard_normal((bits, d), dtype=np.float32)
+
+
+def small_integer_points(n: int, d: int, seed: int = SEED_DATA) -> np.ndarray:
+    """float32 [n][d] with integer values in [-8, 8]; rows are drawn around
+    n / 64 + 1 integer centres (each row: a centre plus an integer offset in
+    [-2, 2] per axis, clipped), so that near neighbours exist."""
+    g = _gen(seed, _S_INT, 0)
+    nc = n // 64 + 1
+    centres = g.integers(-6, 7, size=(nc, d))
+    pick = g.integers(0, nc, size=n)
+    off = g.integers(-2, 3, size=(n, d))
+    return np.clip(centres[pick] + off, -8, 8).astype(np.float32)
+
+
+def small_integer_projection(bits: int, d: int, seed: int = SEED_SKETCH) -> np.ndarray:
+    """float32 [bits][d] with integer values in [-2, 2]."""
+    return _gen(seed, _S_INT, 1).integers(-2, 3, size=(bits, d)).astype(np.float32)
