@@ -173,6 +173,30 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
 int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
                      int32_t* out_idx, float* out_dist, void* stream);
 
+/* ---- second stage: binary sketches ----------------------------------------
+ * The paper filters the forest's candidates by the Hamming distance of 384-bit
+ * sketches before the final vector distances (Section 3 index structure;
+ * Algorithm 1 and Algorithm 2, second-stage filtering). It does not say how
+ * the sketches are made; here bit j of point i is (<x_i, r_j> > 0) for the
+ * rows r_j of a caller-supplied projection matrix R (sign random projection),
+ * computed from the BF16-rounded x and R with FP32 accumulation on the tensor
+ * cores. With hf_set_option mode=3 ("sketch form") hf_knn_graph keeps, per
+ * point, the sketch_k2 candidates of smallest Hamming distance (ties by
+ * index) over all trees' windows, then the k nearest of those by exact
+ * float32 distance (w <= HF_PLAIN_MAX_W).
+ */
+
+/*
+ * hf_set_sketch -- sketches of all points: R is bits x d float32 row-major
+ * (host or device), bits a multiple of 64 in [64, 1024]. Replaces earlier
+ * sketches. HF_EINVAL on bad arguments.
+ */
+int hf_set_sketch(hf_forest* f, const float* R, int32_t bits, void* stream);
+
+/* hf_debug_sketch -- the sketches, n x bits/64 uint64 (bit j of point i is
+ * bit j % 64 of word j / 64); HF_ESTATE before hf_set_sketch. */
+int hf_debug_sketch(hf_forest* f, uint64_t* out, void* stream);
+
 /* ---- learned per-point budget ---------------------------------------------
  * The paper spends one budget -- the number of sorts T and the window k1
  * around each position (Algorithm 2; Table 2 trades recall against it) -- on
@@ -291,8 +315,12 @@ const char* hf_status_string(int status);
  *   to two or more stages of 256 rows, which holds up to d = 512 in mode 1
  *   and d = 896 in mode 2 (hf_get_timings slot 8 reports the form that
  *   ran); they return HF_ENOTIMPL when k + slack > 32;
+ *   mode=3  sketch form: Hamming screen of binary sketches (hf_set_sketch
+ *           first, HF_ESTATE otherwise), then the exact float32 re-rank;
  *   tensor_slack=S  in modes 1 and 2, keep k + S candidates per point for
  *           the re-rank (rounded up to 16 or 32; default S = 1);
+ *   sketch_k2=K2  in mode 3, candidates kept by Hamming distance (1..64,
+ *           default 60; at least k are kept);
  *   timing=1  record per-phase CUDA-event timings (default 1).
  * Unknown keys or values give HF_EINVAL.
  */
@@ -305,7 +333,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
  * 1), [5] search, [6] number of kernel launches of the last build (as a
  * float), [7] re-rank (modes 1, 2), [8] the form the last hf_knn_graph ran
  * (0 = plain float32 window kernel, 1 = BF16 tensor-core Gram bands, 2 = FP8
- * e4m3 Gram bands), so a caller that asked for a tensor form can see whether
+ * e4m3 Gram bands, 3 = sketch form), so a caller that asked for a tensor form can see whether
  * it fell back, [9] the part of [4] spent gathering each tree's rows into its
  * order (tensor forms), [10..11] reserved (0). Writes min(cap, 12).
  */

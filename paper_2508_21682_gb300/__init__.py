@@ -33,6 +33,7 @@ SYMBOLS = [
     "hf_launch_count", "hf_search_static", "hf_trim_pool",
     "hf_budget_labels", "hf_knn_graph_budget", "hf_mlp_create", "hf_mlp_free", "hf_mlp_param_count",
     "hf_mlp_get_params", "hf_mlp_set_params", "hf_mlp_predict", "hf_mlp_grads", "hf_mlp_train",
+    "hf_set_sketch", "hf_debug_sketch",
 ]
 
 _lib = None
@@ -83,6 +84,8 @@ def lib() -> ctypes.CDLL:
         "hf_mlp_predict": [vp, vp, i64, vp, vp],
         "hf_mlp_grads": [vp, vp, vp, i32, vp, vp, vp],
         "hf_mlp_train": [vp, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp],
+        "hf_set_sketch": [vp, vp, i32, vp],
+        "hf_debug_sketch": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -274,6 +277,20 @@ class Forest:
         _check(lib().hf_budget_labels(self._h, kp, k, tg.ctypes.data, len(tg), wg.ctypes.data, len(wg), min_hits,
                                       op, cp, _stream(knn)), "hf_budget_labels")
         return out_targets, out_cell
+
+    def set_sketch(self, R):
+        """hf_set_sketch: sketches of all points from the projection R
+        (bits x d float32, CUDA tensor or numpy)."""
+        if R.ndim != 2 or R.shape[1] != self.d or str(R.dtype).split(".")[-1] != "float32":
+            raise ValueError("R must be float32 of shape (bits, d)")
+        rp, _r = _ptr(R)
+        _check(lib().hf_set_sketch(self._h, rp, R.shape[0], _stream(R)), "hf_set_sketch")
+        self.sketch_bits = int(R.shape[0])
+
+    def sketches(self):
+        out = np.empty((self.n, self.sketch_bits // 64), np.uint64)
+        _check(lib().hf_debug_sketch(self._h, out.ctypes.data, None), "hf_debug_sketch")
+        return out
 
     def set_option(self, key: str, value: int):
         _check(lib().hf_set_option(self._h, key.encode(), value), "hf_set_option")

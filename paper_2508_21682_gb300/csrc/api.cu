@@ -156,6 +156,7 @@ void destroy(hf_forest* f, cudaStream_t s) {
   dfree(f->err, s);
   dfree(f->xb, s);
   dfree(f->xmeta, s);
+  dfree(f->sketch, s);
   delete f;
 }
 
@@ -473,8 +474,11 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
   if (!f || !key) return HF_EINVAL;
   std::string k(key);
   if (k == "mode") {
-    if (value < 0 || value > 2) return HF_EINVAL;
+    if (value < 0 || value > 3) return HF_EINVAL;
     f->mode = (int)value;
+  } else if (k == "sketch_k2") {
+    if (value < 1 || value > HF_MAX_K) return HF_EINVAL;
+    f->sketch_k2 = (int)value;
   } else if (k == "tensor_slack") {
     if (value < -1 || value > 64) return HF_EINVAL;
     f->tensor_slack = (int)value;
@@ -515,13 +519,16 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   // float32 distance. Tensor mode: the Gram kernel keeps the top kp >= k + 1
   // (by default) by the BF16 expansion, then the re-rank orders them by exact
   // float32 distance. Either way the first k columns are the result.
-  const int form = f->mode >= 1 && gram_supported(f->d, w, f->mode) ? f->mode : 0;
-  const bool tensor = form != 0;
+  // form: 0 plain, 1 BF16 Gram, 2 FP8 Gram, 3 sketches (Hamming screen)
+  const int form = f->mode == 3 ? 3 : (f->mode >= 1 && gram_supported(f->d, w, f->mode) ? f->mode : 0);
+  const bool tensor = form == 1 || form == 2;
+  const bool sketchf = form == 3;
+  if (sketchf && !f->sketch) return HF_ESTATE;            // hf_set_sketch first
   if (!tensor && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;  // widest window the plain band launches cover
   if (!tensor && budget) return HF_ENOTIMPL;              // per-point windows: tensor forms only
   f->timings[8] = (float)form;  // the form that runs
   const int slack = f->tensor_slack < 0 ? 1 : f->tensor_slack;
-  const int kp = window_list_pitch(tensor ? k + slack : k);
+  const int kp = window_list_pitch(tensor ? k + slack : (sketchf ? (f->sketch_k2 > k ? f->sketch_k2 : k) : k));
   if (tensor && kp > 32) return HF_ENOTIMPL;  // tensor lists hold at most 32 entries
   uint32_t* li = nullptr;
   float* ldd = nullptr;
@@ -568,11 +575,15 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
       cudaEvent_t g1 = tm.mark();
       tm.span(9, g0, g1);
       rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs, ms, s);
+    } else if (sketchf) {
+      rc = launch_window_hamming(reinterpret_cast<const uint32_t*>(f->sketch), n, f->sketch_bits / 32,
+                                 f->sigma + (size_t)t * n, w, kp, li, ldd, s);
     } else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
   }
   cudaEvent_t a1 = tm.mark();
-  if (rc == HF_OK && tensor) rc = launch_rerank(f->x, n, f->d, f->sigma, kp, li, ldd, s);
+  if (rc == HF_OK && (tensor || sketchf))
+    rc = launch_rerank(f->x, n, f->d, f->sigma, kp, sketchf ? (f->sketch_k2 > k ? f->sketch_k2 : k) : kp, li, ldd, s);
   cudaEvent_t a2 = tm.mark();
   tm.span(4, a0, a1);
   tm.span(7, a1, a2);
@@ -623,6 +634,54 @@ int hf_knn_graph_budget(hf_forest* f, int32_t k, const int32_t* w_pt, const int3
     return HF_EINVAL;
   if (classify(w_pt) != 1 || classify(T_pt) != 1) return HF_EINVAL;
   return knn_graph_impl(f, k, w_max, w_pt, T_pt, T_max, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+int hf_set_sketch(hf_forest* f, const float* R, int32_t bits, void* stream) {
+  if (!f || !R || bits < 64 || bits > 1024 || bits % 64) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  const int d = f->d, dp = (d + 63) / 64 * 64;
+  const int64_t n = f->n;
+  float* rd = nullptr;
+  void *rb = nullptr, *xbt = nullptr;
+  uint64_t* sk = nullptr;
+  cudaError_t e = cudaSuccess;
+  const bool dev_r = classify(R) == 1;
+  if (!dev_r) e = dalloc(&rd, (size_t)bits * d, s);
+  if (e == cudaSuccess) e = dalloc_bytes(&rb, (size_t)bits * dp * 2, s);
+  if (e == cudaSuccess) e = dalloc_bytes(&xbt, (size_t)n * dp * 2, s);
+  if (e == cudaSuccess) e = dalloc(&sk, (size_t)n * (bits / 64), s);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) {
+    if (!dev_r) cudaMemcpyAsync(rd, R, (size_t)bits * d * 4, cudaMemcpyHostToDevice, s);
+    launch_f32_to_bf16(dev_r ? R : rd, bits, d, dp, rb, s);
+    launch_f32_to_bf16(f->x, n, d, dp, xbt, s);
+    rc = launch_sketch(xbt, n, dp, rb, bits, sk, f->err, s);
+  }
+  const int rc2 = finish(f, s);
+  if (rc == HF_OK) rc = rc2;
+  dfree(rd, s);
+  dfree(rb, s);
+  dfree(xbt, s);
+  if (rc == HF_OK) {
+    dfree(f->sketch, s);
+    f->sketch = sk;
+    f->sketch_bits = bits;
+  } else {
+    dfree(sk, s);
+  }
+  return rc;
+}
+
+int hf_debug_sketch(hf_forest* f, uint64_t* out, void* stream) {
+  if (!f || !out) return HF_EINVAL;
+  if (!f->sketch) return HF_ESTATE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  const int rc = map_cuda(cudaMemcpyAsync(out, f->sketch, (size_t)f->n * (f->sketch_bits / 64) * 8,
+                                          cudaMemcpyDefault, s));
+  const int rc2 = finish(f, s);
+  return rc != HF_OK ? rc : rc2;
 }
 
 int hf_budget_labels(hf_forest* f, const int32_t* knn, int32_t k, const int32_t* t_grid, int32_t nt,

@@ -52,7 +52,10 @@ bool on_device(const void* p) {
 // every thread waits on (bounded) before the next chunk; the epilogue reads
 // the accumulator (warp w: rows 32 w .. 32 w + 31) 16 columns at a time.
 // ---------------------------------------------------------------------------
-enum { EPI_STORE = 0, EPI_BIAS_GELU = 1, EPI_BIAS = 2 };
+// EPI_SIGN: bit j of row m = (C[m][j] > 0), 16 bits per uint16 of the
+// output row (the sketch of the second stage); C is the uint16 output and
+// ldc its row pitch in uint16 units.
+enum { EPI_STORE = 0, EPI_BIAS_GELU = 1, EPI_BIAS = 2, EPI_SIGN = 3 };
 
 struct GemmArgs {
   const __nv_bfloat16* A;
@@ -138,7 +141,12 @@ __global__ void __launch_bounds__(128, 1) mlp_gemm_kernel(GemmArgs g) {
     for (int c = 0; c < nt; c += 16) {
       uint32_t v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      if (m < g.M) {
+      if (m < g.M && EPI == EPI_SIGN) {
+        uint32_t bitsv = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) bitsv |= (__uint_as_float(v[j]) > 0.f ? 1u : 0u) << j;
+        reinterpret_cast<uint16_t*>(g.C)[(size_t)m * g.ldc + (n0 + c) / 16] = (uint16_t)bitsv;
+      } else if (m < g.M) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c + j;
@@ -163,7 +171,7 @@ constexpr size_t GEMM_SMEM = 16384 + 256 * 128 + 1024;
 template <int EPI>
 int gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K, int nt, float* C,
          int ldc, const float* bias, __nv_bfloat16* H, int ldh, int* err, cudaStream_t s) {
-  if (M % 128 || K % 64 || N % 16 || nt % 16 || nt > 256 || N % nt) return HF_EINVAL;
+  if (M < 1 || K % 64 || N % 16 || nt % 16 || nt > 256 || N % nt) return HF_EINVAL;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute((const void*)mlp_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -172,7 +180,7 @@ int gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M
     attr = true;
   }
   GemmArgs g{A, B, lda, ldb, M, N, K, nt, C, ldc, bias, H, ldh, err};
-  mlp_gemm_kernel<EPI><<<dim3(M / 128, N / nt), 128, GEMM_SMEM, s>>>(g);
+  mlp_gemm_kernel<EPI><<<dim3((M + 127) / 128, N / nt), 128, GEMM_SMEM, s>>>(g);
   hf_after_launch("mlp_gemm_kernel", s);
   return HF_OK;
 }
@@ -828,4 +836,20 @@ void launch_tree_budget(const uint32_t* sigma, int64_t n, int t, const int32_t* 
                         int32_t* tile_w, cudaStream_t s) {
   tree_budget_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(sigma, n, t, wpt, tpt, pw, tile_w);
   hf_after_launch("tree_budget_kernel", s);
+}
+
+// Sketches: bit j of point i = (<x_i, r_j> > 0) for the rows r_j of R, from
+// the BF16 copies (xb: n x dp, rb: bits x dp), FP32 accumulation.
+int launch_sketch(const void* xb, int64_t n, int dp, const void* rb, int bits, uint64_t* sketch, int* err,
+                  cudaStream_t s) {
+  if (bits < 64 || bits % 64 || bits > 1024 || n > (int64_t)1 << 30) return HF_EINVAL;
+  const int nt = bits % 256 == 0 ? 256 : (bits % 128 == 0 ? 128 : 64);
+  return gemm<EPI_SIGN>(static_cast<const __nv_bfloat16*>(xb), dp, static_cast<const __nv_bfloat16*>(rb), dp, (int)n,
+                        bits, dp, nt, reinterpret_cast<float*>(sketch), bits / 16, nullptr, nullptr, 0, err, s);
+}
+
+void launch_f32_to_bf16(const float* x, int64_t rows, int cols, int ld, void* out, cudaStream_t s) {
+  f32_to_bf16_kernel<<<hf_blocks(rows * ld, 256, 152 * 8), 256, 0, s>>>(x, rows, cols, ld,
+                                                                        static_cast<__nv_bfloat16*>(out), ld);
+  hf_after_launch("f32_to_bf16_kernel", s);
 }

@@ -750,10 +750,11 @@ __device__ __forceinline__ float warp_transpose_sum(float (&v)[NV], int lane) {
 // in coalesced 512-byte pieces when rows are float4-aligned) and keeps one
 // partial sum per candidate; a transposing butterfly gives candidate j's
 // distance in lane j. The KP entries are then re-sorted by (distance, index);
-// empty slots stay (+inf, 0xffffffff).
+// empty slots stay (+inf, 0xffffffff). Slots kc.. of the incoming list are
+// dropped (kc = KP keeps all).
 template <int KP>
 __global__ void __launch_bounds__(256, 6) rerank_kernel(const float* __restrict__ x, int64_t n, int d,
-                                                     const uint32_t* __restrict__ order, int vec4,
+                                                     const uint32_t* __restrict__ order, int vec4, int kc,
                                                      uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
   constexpr int PER = (KP + 31) / 32;
   constexpr int NV = KP < 32 ? KP : 32;  // candidates per round
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(256, 6) rerank_kernel(const float* __restrict_
   uint32_t id[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    id[u] = 32 * u + lane < KP ? lidx[(size_t)i * KP + 32 * u + lane] : 0xffffffffu;
+    id[u] = 32 * u + lane < kc ? lidx[(size_t)i * KP + 32 * u + lane] : 0xffffffffu;
     dd[u] = INFINITY;
   }
 #pragma unroll
@@ -1009,14 +1010,15 @@ int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w,
   }
 }
 
-int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
+int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, int kc, uint32_t* li, float* ld,
                   cudaStream_t s) {
   const unsigned blocks = hf_blocks(n * 32, 256);
   const int vec4 = d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  if (kc < 1 || kc > kp) return HF_EINVAL;
   switch (kp) {
-    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
-    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
-    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, li, ld); break;
+    case 16: rerank_kernel<16><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, kc, li, ld); break;
+    case 32: rerank_kernel<32><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, kc, li, ld); break;
+    case 64: rerank_kernel<64><<<blocks, 256, 0, s>>>(x, n, d, order, vec4, kc, li, ld); break;
     default: return HF_EINVAL;
   }
   hf_after_launch("rerank_kernel", s);

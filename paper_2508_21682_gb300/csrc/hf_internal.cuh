@@ -68,6 +68,9 @@ struct hf_forest {
   void* xb = nullptr;
   float2* xmeta = nullptr;
   int xform = 0;  // form of xb: 0 none, 1 BF16, 2 FP8
+  // second stage: binary sketches (n x sketch_bits / 64 words)
+  uint64_t* sketch = nullptr;
+  int sketch_bits = 0;
 
   uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
   uint32_t* p0t = nullptr;    // [ceil(n/32)][d] bit-sliced plane 0 (scratch, top-level prefix path)
@@ -81,6 +84,7 @@ struct hf_forest {
   int sort_batch_max = 0;  // cap on trees per sort batch (0: by memory)
   int mode = 0;
   int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
+  int sketch_k2 = 60;     // candidates kept by Hamming distance (mode 3)
   int timing = 1;
 
   float timings[HF_NTIMINGS] = {0};
@@ -123,6 +127,9 @@ int window_list_pitch(int k);  // list slots per point kept by the window kernel
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s);
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
+// the same over binary sketches (words 32-bit words per point), Hamming distance
+int launch_window_hamming(const uint32_t* sketch, int64_t n, int words, const uint32_t* sigma, int w, int kp,
+                          uint32_t* list_idx, float* list_dist, cudaStream_t s);
 
 // gram.cu -- tensor-core window distances. form 1: BF16 operands; form 2:
 // FP8 e4m3 operands with one scale per vector.
@@ -142,7 +149,8 @@ void launch_gather_rows(const void* xq, const float2* meta, int form, int64_t n,
 int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w, const int32_t* tile_w,
                        const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err, const void* xs, const float2* ms,
                        cudaStream_t s);
-int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, uint32_t* li, float* ld,
+// exact float32 re-rank of the first kc slots of each KP-slot list
+int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, int kc, uint32_t* li, float* ld,
                   cudaStream_t s);
 
 // budget.cu
@@ -154,6 +162,13 @@ int launch_budget_labels(const uint32_t* sigma, int T, int64_t n, const int32_t*
 // largest windows tile_w from per-point (w, T) budgets
 void launch_tree_budget(const uint32_t* sigma, int64_t n, int t, const int32_t* wpt, const int32_t* tpt, uint16_t* pw,
                         int32_t* tile_w, cudaStream_t s);
+
+// sketches (budget.cu): bit j of point i = (<x_i, r_j> > 0); xb and rb BF16
+// with row pitch dp (a multiple of 64); sketch n x bits/64 words
+int launch_sketch(const void* xb, int64_t n, int dp, const void* rb, int bits, uint64_t* sketch, int* err,
+                  cudaStream_t s);
+// rows x cols float32 (pitch cols) -> rows x ld BF16 (zero padded)
+void launch_f32_to_bf16(const float* x, int64_t rows, int cols, int ld, void* out, cudaStream_t s);
 
 // search.cu
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,

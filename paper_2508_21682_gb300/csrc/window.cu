@@ -86,7 +86,10 @@ __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const u
 
 
 // One band of offsets [dlo, dlo + WB - 1] for the block's positions.
-template <int KP, int NT>
+// HAM: the rows are binary sketches (d 32-bit words each) and the distance is
+// their Hamming distance (the paper's second-stage filter); otherwise float32
+// squared Euclidean distance with exact coordinate differences.
+template <int KP, int NT, bool HAM>
 __global__ void __launch_bounds__(NT, 512 / NT)
 window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sigma, int w,
               int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
@@ -143,8 +146,14 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
       for (int t = 0; t < UR; ++t)
 #pragma unroll
         for (int c = 0; c < UC; ++c) {
-          const float e = a[t] - b[1 + t + c];
-          acc[t][c] = fmaf(e, e, acc[t][c]);
+          if (HAM) {
+            // integer popcount sums kept in the float registers' bits
+            const uint32_t xr = __float_as_uint(a[t]) ^ __float_as_uint(b[1 + t + c]);
+            acc[t][c] = __uint_as_float(__float_as_uint(acc[t][c]) + (uint32_t)__popc(xr));
+          } else {
+            const float e = a[t] - b[1 + t + c];
+            acc[t][c] = fmaf(e, e, acc[t][c]);
+          }
         }
     }
     __syncthreads();
@@ -156,7 +165,8 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
 #pragma unroll
   for (int t = 0; t < UR; ++t)
 #pragma unroll
-    for (int c = 0; c < UC; ++c) band[(pr + t) * WB + UC * o + c] = acc[t][c];
+    for (int c = 0; c < UC; ++c)
+      band[(pr + t) * WB + UC * o + c] = HAM ? (float)__float_as_uint(acc[t][c]) : acc[t][c];
   __syncthreads();
 
   // merge: positions s + tt, tt < B; the point's list is held in registers
@@ -192,28 +202,28 @@ size_t window_smem(int B, int dhi, int rows) {
   return ((staging > bandf ? staging : bandf) + (size_t)NR) * 4;
 }
 
-template <int KP, int NT>
+template <int KP, int NT, bool HAM>
 int launch_band(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int dlo, uint32_t* li, float* ldd,
                 cudaStream_t s) {
   const int dhi = dlo + WB - 1;
   const int B = rows_of(NT) - dhi;
   const size_t smem = window_smem(B, dhi, rows_of(NT));
   if (B < 32 || smem > 227 * 1024) return HF_ENOTIMPL;
-  if (cudaFuncSetAttribute((const void*)window_kernel<KP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute((const void*)window_kernel<KP, NT, HAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
-  window_kernel<KP, NT><<<hf_blocks(n, B), NT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
-  hf_after_launch("window_kernel", s);
+  window_kernel<KP, NT, HAM><<<hf_blocks(n, B), NT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
+  hf_after_launch(HAM ? "window_kernel<hamming>" : "window_kernel", s);
   return HF_OK;
 }
 
-template <int KP>
+template <int KP, bool HAM>
 int launch_kp(const float* x, int64_t n, int d, const uint32_t* sigma, int w, uint32_t* li, float* ldd,
               cudaStream_t s) {
   for (int dlo = 1; dlo <= w; dlo += WB) {
     const int dhi = dlo + WB - 1;
-    const int rc = rows_of(256) - dhi >= 32 ? launch_band<KP, 256>(x, n, d, sigma, w, dlo, li, ldd, s)
-                                            : launch_band<KP, 512>(x, n, d, sigma, w, dlo, li, ldd, s);
+    const int rc = rows_of(256) - dhi >= 32 ? launch_band<KP, 256, HAM>(x, n, d, sigma, w, dlo, li, ldd, s)
+                                            : launch_band<KP, 512, HAM>(x, n, d, sigma, w, dlo, li, ldd, s);
     if (rc != HF_OK) return rc;
   }
   return HF_OK;
@@ -234,9 +244,20 @@ int window_list_pitch(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
                         uint32_t* list_idx, float* list_dist, cudaStream_t s) {
   switch (kp) {
-    case 16: return launch_kp<16>(x, n, d, sigma, w, list_idx, list_dist, s);
-    case 32: return launch_kp<32>(x, n, d, sigma, w, list_idx, list_dist, s);
-    case 64: return launch_kp<64>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 16: return launch_kp<16, false>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 32: return launch_kp<32, false>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 64: return launch_kp<64, false>(x, n, d, sigma, w, list_idx, list_dist, s);
+    default: return HF_EINVAL;
+  }
+}
+
+int launch_window_hamming(const uint32_t* sketch, int64_t n, int words, const uint32_t* sigma, int w, int kp,
+                          uint32_t* list_idx, float* list_dist, cudaStream_t s) {
+  const float* x = reinterpret_cast<const float*>(sketch);  // staged as raw 32-bit words
+  switch (kp) {
+    case 16: return launch_kp<16, true>(x, n, words, sigma, w, list_idx, list_dist, s);
+    case 32: return launch_kp<32, true>(x, n, words, sigma, w, list_idx, list_dist, s);
+    case 64: return launch_kp<64, true>(x, n, words, sigma, w, list_idx, list_dist, s);
     default: return HF_EINVAL;
   }
 }
