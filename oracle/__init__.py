@@ -15,7 +15,7 @@ from .hilbert_forest import *  # noqa: F401,F403
 from .hilbert_forest import (  # noqa: F401
     Forest, SplitMix64, axis_range, brute_force_knn, candidate_sets, hilbert_keys,
     hilbert_order, key_less_count, key_words, knn_graph, locate, pack_key,
-    permute_reflect, quantize, query_codes, recall, search, skilling_transpose,
+    permute_reflect, quantize, query_codes, recall, search, search_candidates, skilling_transpose,
     sq_dist_fp64, topk_from_candidates, tree_params, window_candidates,
 )
 from . import budget  # noqa: F401,E402  (learned per-point budget: labels, MLP, budgeted graph)

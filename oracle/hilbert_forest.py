@@ -367,6 +367,15 @@ def search(forest: Forest, queries: np.ndarray, k: int, w: int):
     query's lower-bound position p (clipped); the result is the k nearest of
     their union by float64 squared distance, ties by index."""
     queries = np.ascontiguousarray(queries, dtype=np.float32)
+    cand = search_candidates(forest, queries, w)
+    return topk_from_candidates(forest.x, None, cand, k, xq=queries)
+
+
+def search_candidates(forest: Forest, queries: np.ndarray, w: int) -> np.ndarray:
+    """The first stage of Algorithm 1: per tree, the points at positions
+    [p - w, p + w) around each query's lower-bound position p (clipped), as an
+    int64 [nq][T * 2w] array with -1 for "none" (repeats across trees kept)."""
+    queries = np.ascontiguousarray(queries, dtype=np.float32)
     qc = query_codes(forest, queries)
     nq = queries.shape[0]
     cols = []
@@ -378,8 +387,7 @@ def search(forest: Forest, queries: np.ndarray, k: int, w: int):
             ok = (pp >= 0) & (pp < forest.n)
             c[ok, j] = forest.sigma[t][pp[ok]]
         cols.append(c)
-    cand = np.concatenate(cols, axis=1)
-    return topk_from_candidates(forest.x, None, cand, k, xq=queries)
+    return np.concatenate(cols, axis=1)
 
 
 # --------------------------------------------------------------------------

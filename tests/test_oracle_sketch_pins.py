@@ -171,3 +171,111 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     xi = np.array([[1.0, -1.0, 0.0] + [0.0] * 61], np.float32)
     assert int(OS.sketches(xi, np.eye(64, dtype=np.float32))[0, 0]) == 1
     assert int(OS.pack_bits(OS.sketch_dots(xi, np.eye(64, dtype=np.float32)) >= 0)[0, 0]) != 1
+
+
+# ---------------------------------------------------------------- search side
+def _brute_search(x, f, queries, sk, qsk, k, w, k2, h):
+    """Pure-Python Algorithm 1 with both filters."""
+    n = x.shape[0]
+    qc = O.query_codes(f, queries)
+    sig0 = [int(v) for v in f.sigma[0]]
+    pos0 = {p: r for r, p in enumerate(sig0)}
+    out = []
+    for j in range(queries.shape[0]):
+        cset = set()
+        for t in range(f.T):
+            p = int(O.locate(f, t, qc[j:j + 1])[0])
+            for q in range(max(0, p - w), min(n, p + w)):
+                cset.add(int(f.sigma[t][q]))
+        def ham(c):
+            return sum(bin(int(qsk[j, u]) ^ int(sk[c, u])).count("1") for u in range(sk.shape[1]))
+        c2 = sorted(cset, key=lambda c: (ham(c), c))[:k2]
+        ex = set()
+        for c in c2:
+            for o in range(-h, h + 1):
+                r = pos0[c] + o
+                if 0 <= r < n:
+                    ex.add(sig0[r])
+        def dist(c):
+            return sum((float(queries[j, m]) - float(x[c, m])) ** 2 for m in range(x.shape[1]))
+        top = sorted(ex, key=lambda c: (dist(c), c))[:k]
+        out.append(top + [-1] * (k - len(top)))
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("k,w,k2,h", [(3, 2, 4, 1), (5, 4, 3, 2), (4, 3, 8, 0), (2, 1, 1, 5)])
+def test_search_equals_brute_force(k, w, k2, h):
+    x, f, sk = _case(n=80, bits=128)
+    R = S.sketch_projection(128, 6, seed=22)
+    q = S.unit_gaussian(12, 6, seed=40)
+    qsk = OS.sketches(q, R)
+    gi, gd = OS.search_sketch(f, q, k, w, sk, qsk, k2, h)
+    assert np.array_equal(gi, _brute_search(x, f, q, sk, qsk, k, w, k2, h))
+    xd, qd = x.astype(np.float64), q.astype(np.float64)
+    for j in range(12):
+        for c in range(k):
+            if gi[j, c] >= 0:
+                assert gd[j, c] == pytest.approx(np.sum((qd[j] - xd[gi[j, c]]) ** 2), rel=1e-12)
+
+
+def test_search_without_filters_is_the_search():
+    """k2 keeping every candidate and h = 0: Algorithm 1's first stage alone."""
+    x, f, sk = _case(n=400, d=8, T=3, bits=64, seed=5)
+    q = S.unit_gaussian(30, 8, seed=41)
+    qsk = OS.sketches(q, S.sketch_projection(64, 8, seed=27))
+    w = 7
+    gi, gd = OS.search_sketch(f, q, 6, w, sk, qsk, k2=2 * w * 3, h=0)
+    ri, rd = O.search(f, q, 6, w)
+    assert np.array_equal(gi, ri) and np.array_equal(gd, rd)
+
+
+def test_search_expansion_over_the_whole_order_is_exact():
+    """h >= n: any one surviving candidate brings every point, so the result
+    is the exact k nearest of each query (brute force)."""
+    x, f, sk = _case(n=150, d=5, T=1, bits=64, seed=6)
+    q = S.unit_gaussian(10, 5, seed=42)
+    qsk = OS.sketches(q, S.sketch_projection(64, 5, seed=28))
+    gi, gd = OS.search_sketch(f, q, 7, 2, sk, qsk, k2=1, h=150)
+    xd, qd = x.astype(np.float64), q.astype(np.float64)
+    for j in range(10):
+        dd = np.sum((xd - qd[j]) ** 2, axis=1)
+        want = np.lexsort((np.arange(150), dd))[:7]
+        assert np.array_equal(gi[j], want)
+
+
+def test_master_expand_positions():
+    x, f, sk = _case(n=50, d=4, T=2, bits=64, seed=7)
+    pos0, sig0 = f.position(0), f.sigma[0]
+    c2 = np.array([[int(sig0[0]), int(sig0[25]), -1]])
+    ex = OS.master_expand(f, c2, 2)
+    # first candidate at position 0: offsets -2, -1 fall off the order
+    assert list(ex[0, :5]) == [-1, -1, int(sig0[0]), int(sig0[1]), int(sig0[2])]
+    assert list(ex[0, 5:10]) == [int(sig0[p]) for p in range(23, 28)]
+    assert np.all(ex[0, 10:] == -1)
+    assert pos0[sig0[25]] == 25
+
+
+def test_planted_expansion_mistakes_fail(monkeypatch):
+    x, f, sk = _case(n=80, bits=128)
+    q = S.unit_gaussian(12, 6, seed=40)
+    qsk = OS.sketches(q, S.sketch_projection(128, 6, seed=22))
+    k, w, k2, h = 4, 3, 3, 2
+    want = _brute_search(x, f, q, sk, qsk, k, w, k2, h)
+    real = OS.master_expand
+
+    def other_order(forest, c2, hh):  # expansion in order 1, not the master order
+        class V:
+            n = forest.n
+            sigma = [forest.sigma[1]]
+            def position(self, t):
+                return forest.position(1)
+        return real(V(), c2, hh)
+
+    def no_centre(forest, c2, hh):  # the candidate itself left out
+        e = real(forest, c2, hh).reshape(c2.shape[0], c2.shape[1], 2 * hh + 1)
+        e[:, :, hh] = -1
+        return e.reshape(c2.shape[0], -1)
+
+    for bad in (other_order, no_centre):
+        monkeypatch.setattr(OS, "master_expand", bad)
+        assert not np.array_equal(OS.search_sketch(f, q, k, w, sk, qsk, k2, h)[0], want), bad.__name__
