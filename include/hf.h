@@ -74,6 +74,7 @@ enum {
 #define HF_MAX_D 4096
 #define HF_MAX_BITS 8
 #define HF_MAX_K 64
+#define HF_MAX_K2 1024 /* sketch_k2 limit of the sketch-form search */
 #define HF_MAX_N (((int64_t)1 << 30) - 1)
 /* Widest window of the plain float32 graph form (hf_set_option mode=0). */
 #define HF_PLAIN_MAX_W 704
@@ -167,7 +168,8 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
  *   - every call uses the same array, overwriting it completely: calls that
  *     overlap on the GPU (other streams, other threads, other forests on the
  *     same device) race on it and must be serialised by the caller.
- * Results, status codes and synchronisation are those of hf_search.
+ * Results, status codes and synchronisation are those of hf_search in modes
+ * 0..2; the sketch form (mode 3) is not run here (HF_ENOTIMPL).
  */
 #define HF_STATIC_QUERY_BYTES (4u << 20)
 int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
@@ -183,7 +185,17 @@ int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, 
  * cores. With hf_set_option mode=3 ("sketch form") hf_knn_graph keeps, per
  * point, the sketch_k2 candidates of smallest Hamming distance (ties by
  * index) over all trees' windows, then the k nearest of those by exact
- * float32 distance (w <= HF_PLAIN_MAX_W).
+ * float32 distance (w <= HF_PLAIN_MAX_W, sketch_k2 <= HF_MAX_K, else
+ * HF_ENOTIMPL). hf_search in mode 3 follows Algorithm 1 with both filters:
+ * each query's sketch (from the same R) against its window candidates of
+ * every tree, the sketch_k2 (<= HF_MAX_K2) of smallest (Hamming distance,
+ * index) survive, each brings the expand_h points on either side of it in the
+ * master order (order 0), and the k nearest of that set by float32 distance
+ * are returned. The first such search keeps a master-ordered copy of the
+ * points (n x d float32) and the inverse of the master order (n x uint32)
+ * until hf_free. hf_search_static does not run the sketch form (HF_ENOTIMPL
+ * in mode 3). hf_set_sketch keeps the BF16 copy of R (bits x 64-padded d)
+ * for the query sketches.
  */
 
 /*
@@ -319,8 +331,11 @@ const char* hf_status_string(int status);
  *           first, HF_ESTATE otherwise), then the exact float32 re-rank;
  *   tensor_slack=S  in modes 1 and 2, keep k + S candidates per point for
  *           the re-rank (rounded up to 16 or 32; default S = 1);
- *   sketch_k2=K2  in mode 3, candidates kept by Hamming distance (1..64,
- *           default 60; at least k are kept);
+ *   sketch_k2=K2  in mode 3, candidates kept by Hamming distance
+ *           (1..HF_MAX_K2, default 60; the graph takes at most HF_MAX_K and
+ *           keeps at least k);
+ *   expand_h=H  in mode 3, master-order neighbours taken on either side of
+ *           each search survivor (default 2);
  *   timing=1  record per-phase CUDA-event timings (default 1).
  * Unknown keys or values give HF_EINVAL.
  */

@@ -157,6 +157,9 @@ void destroy(hf_forest* f, cudaStream_t s) {
   dfree(f->xb, s);
   dfree(f->xmeta, s);
   dfree(f->sketch, s);
+  dfree(f->sketch_r, s);
+  dfree(f->xm, s);
+  dfree(f->posm, s);
   delete f;
 }
 
@@ -477,8 +480,11 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value) {
     if (value < 0 || value > 3) return HF_EINVAL;
     f->mode = (int)value;
   } else if (k == "sketch_k2") {
-    if (value < 1 || value > HF_MAX_K) return HF_EINVAL;
+    if (value < 1 || value > HF_MAX_K2) return HF_EINVAL;
     f->sketch_k2 = (int)value;
+  } else if (k == "expand_h") {
+    if (value < 0 || value > (1 << 20)) return HF_EINVAL;
+    f->expand_h = (int)value;
   } else if (k == "tensor_slack") {
     if (value < -1 || value > 64) return HF_EINVAL;
     f->tensor_slack = (int)value;
@@ -524,6 +530,7 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   const bool tensor = form == 1 || form == 2;
   const bool sketchf = form == 3;
   if (sketchf && !f->sketch) return HF_ESTATE;            // hf_set_sketch first
+  if (sketchf && f->sketch_k2 > HF_MAX_K) return HF_ENOTIMPL;  // the band lists hold at most 64
   if (!tensor && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;  // widest window the plain band launches cover
   if (!tensor && budget) return HF_ENOTIMPL;              // per-point windows: tensor forms only
   f->timings[8] = (float)form;  // the form that runs
@@ -661,14 +668,16 @@ int hf_set_sketch(hf_forest* f, const float* R, int32_t bits, void* stream) {
   const int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
   dfree(rd, s);
-  dfree(rb, s);
   dfree(xbt, s);
   if (rc == HF_OK) {
     dfree(f->sketch, s);
+    dfree(f->sketch_r, s);
     f->sketch = sk;
+    f->sketch_r = rb;
     f->sketch_bits = bits;
   } else {
     dfree(sk, s);
+    dfree(rb, s);
   }
   return rc;
 }
@@ -717,6 +726,47 @@ int hf_budget_labels(hf_forest* f, const int32_t* knn, int32_t k, const int32_t*
   return rc != HF_OK ? rc : rc2;
 }
 
+// Sketch form of the search (Algorithm 1 with both filters): positions of
+// every tree, query sketches, then one warp per query for the Hamming stage,
+// the master-order expansion and the final float32 stage. The master-ordered
+// copy of the points is built on the first such call and kept.
+static int sketch_search(hf_forest* f, const float* q, const uint8_t* qc, int64_t nq, int k, int w, uint32_t* li,
+                         float* ldd, cudaStream_t s) {
+  if (!f->sketch || !f->sketch_r) return HF_ESTATE;
+  if (!f->sigma) return HF_ESTATE;
+  const int d = f->d, dp = (d + 63) / 64 * 64, words = f->sketch_bits / 64;
+  cudaError_t e = cudaSuccess;
+  if (!f->xm) {
+    e = dalloc(&f->xm, (size_t)f->n * d, s);
+    if (e == cudaSuccess) e = dalloc(&f->posm, (size_t)f->n, s);
+    if (e != cudaSuccess) {
+      dfree(f->xm, s);
+      dfree(f->posm, s);
+      f->xm = nullptr;
+      f->posm = nullptr;
+      return map_cuda(e);
+    }
+    launch_master_layout(f->x, f->n, d, f->sigma, f->xm, f->posm, s);
+  }
+  int64_t* pos = nullptr;
+  void* qb = nullptr;
+  uint64_t* qsk = nullptr;
+  e = dalloc(&pos, (size_t)f->T * nq, s);
+  if (e == cudaSuccess) e = dalloc_bytes(&qb, (size_t)nq * dp * 2, s);
+  if (e == cudaSuccess) e = dalloc(&qsk, (size_t)nq * words, s);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) rc = launch_search(f, q, qc, nq, k, w, nullptr, nullptr, pos, -2, s);
+  if (rc == HF_OK) {
+    launch_f32_to_bf16(q, nq, d, dp, qb, s);
+    rc = launch_sketch(qb, nq, dp, f->sketch_r, f->sketch_bits, qsk, f->err, s);
+  }
+  if (rc == HF_OK) rc = launch_sketch_search(f, q, nq, pos, qsk, k, w, f->sketch_k2, f->expand_h, li, ldd, s);
+  dfree(pos, s);
+  dfree(qb, s);
+  dfree(qsk, s);
+  return rc;
+}
+
 int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w, int32_t* out_idx,
               float* out_dist, void* stream) {
   if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
@@ -744,7 +794,10 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
     const float* qsrc = dev_q ? queries : qd;
     cudaEvent_t a0 = tm.mark();
     launch_quantize_codes(qsrc, nq, d, f->lo, f->scale, f->bits, qc, f->err, s);
-    if (rc == HF_OK) rc = launch_search(f, qsrc, qc, nq, k, w, li, ldd, nullptr, -1, s);
+    if (rc == HF_OK && f->mode == 3)
+      rc = sketch_search(f, qsrc, qc, nq, k, w, li, ldd, s);
+    else if (rc == HF_OK)
+      rc = launch_search(f, qsrc, qc, nq, k, w, li, ldd, nullptr, -1, s);
     cudaEvent_t a1 = tm.mark();
     tm.span(5, a0, a1);
     if (rc == HF_OK && !dev_i) rc = map_cuda(cudaMemcpyAsync(out_idx, li, cnt * 4, cudaMemcpyDeviceToHost, s));

@@ -71,6 +71,9 @@ struct hf_forest {
   // second stage: binary sketches (n x sketch_bits / 64 words)
   uint64_t* sketch = nullptr;
   int sketch_bits = 0;
+  void* sketch_r = nullptr;   // BF16 projection (bits x dp) for query sketches
+  float* xm = nullptr;        // master-ordered points (n x d), built on demand
+  uint32_t* posm = nullptr;   // inverse of the master order
 
   uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
   uint32_t* p0t = nullptr;    // [ceil(n/32)][d] bit-sliced plane 0 (scratch, top-level prefix path)
@@ -85,6 +88,7 @@ struct hf_forest {
   int mode = 0;
   int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
   int sketch_k2 = 60;     // candidates kept by Hamming distance (mode 3)
+  int expand_h = 2;       // master-order neighbours per survivor (mode 3 search)
   int timing = 1;
 
   float timings[HF_NTIMINGS] = {0};
@@ -174,6 +178,12 @@ void launch_f32_to_bf16(const float* x, int64_t rows, int cols, int ld, void* ou
 int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int64_t nq, int k,
                   int w, uint32_t* out_idx, float* out_dist, int64_t* out_pos, int only_tree,
                   cudaStream_t s);
+// sketch form of the search: positions of every tree (pos, T x nq) and query
+// sketches (qsk) first; needs f->sketch, f->xm and f->posm
+int launch_sketch_search(const hf_forest* f, const float* q, int64_t nq, const int64_t* pos, const uint64_t* qsk,
+                         int k, int w, int k2, int h, uint32_t* out_idx, float* out_dist, cudaStream_t s);
+void launch_master_layout(const float* x, int64_t n, int d, const uint32_t* sig0, float* xm, uint32_t* posm,
+                          cudaStream_t s);
 
 // host helpers (api.cu)
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);

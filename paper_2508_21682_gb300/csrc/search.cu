@@ -92,6 +92,7 @@ struct SearchArgs {
   float* out_dist;
   int64_t* out_pos;
   int only_tree;
+  int pos_all;  // positions of every tree into out_pos[t * nq + query], no lists
   int vec4;  // d % 4 == 0 and both matrices 16-byte aligned
   int top;   // the K prefix words lie in the top bit level (d >= 64K)
 };
@@ -312,8 +313,8 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
       }
       pos = __shfl_sync(FULL, pos, 0);
     }
-    if (a.only_tree >= 0) {
-      if (lane == 0) a.out_pos[qi] = pos;
+    if (a.only_tree >= 0 || a.pos_all) {
+      if (lane == 0) a.out_pos[a.pos_all ? (size_t)t * a.nq + qi : (size_t)qi] = pos;
       continue;
     }
     const int64_t c0 = pos - a.w > 0 ? pos - a.w : 0;
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(SWARPS * 32) search_kernel(SearchArgs a) {
       }
     }
   }
-  if (a.only_tree >= 0) return;
+  if (a.only_tree >= 0 || a.pos_all) return;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e = 32 * s + lane;
@@ -433,7 +434,9 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
   a.out_idx = out_idx;
   a.out_dist = out_dist;
   a.out_pos = out_pos;
-  a.only_tree = only_tree;
+  a.only_tree = only_tree >= 0 ? only_tree : -1;
+  a.pos_all = only_tree == -2;
+  if (a.pos_all && !out_pos) return HF_EINVAL;
   a.vec4 = (f->d % 4 == 0) && ((reinterpret_cast<uintptr_t>(f->x) & 15) == 0) &&
            ((reinterpret_cast<uintptr_t>(q) & 15) == 0);
   a.top = f->d >= 64 * f->K;
@@ -441,6 +444,248 @@ int launch_search(const hf_forest* f, const float* q, const uint8_t* qcodes, int
   const int rc = k <= 32 ? launch_s<1>(a, smem, s) : launch_s<2>(a, smem, s);
   if (rc != HF_OK) return rc;
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Search with the second-stage filter and the master-order expansion
+// (Algorithm 1, both filters).
+//
+// One warp per query, after the positions of every tree are known:
+//  * Hamming stage: the window candidates of each tree go 32 at a time, one
+//    per lane; a lane XORs its candidate's sketch with the query's (held in
+//    shared memory) and counts the bits; the 32 counts are sorted across the
+//    warp and merged into a warp-held list of the k2 smallest (Hamming
+//    distance, index), duplicates across trees dropped on insertion.
+//  * Expansion: entry e of the expanded set is survivor e / (2h + 1) shifted by
+//    e % (2h + 1) - h positions in the master order (order 0), clipped. The
+//    rows come from the master-ordered copy of the points, so the 2h + 1 rows
+//    of one survivor are adjacent in memory.
+//  * Final stage: the expanded entries are scored with the same float32
+//    exact-difference distance and transposing butterfly as the plain search
+//    and merged into the warp-held top-k list.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int SK_MAX_WORDS = 16;  // sketches up to 1024 bits
+
+struct SketchSearchArgs {
+  const float* q;
+  int64_t nq;
+  int d;
+  const float* xm;         // n x d, row p = point sig0[p]
+  const uint32_t* sig0;    // master order
+  const uint32_t* posm;    // inverse of the master order
+  const uint32_t* sigma;   // T x n orders
+  const int64_t* pos;      // T x nq lower-bound positions
+  const uint64_t* sk;      // n x words
+  const uint64_t* qsk;     // nq x words
+  int words;
+  int64_t n;
+  int T, w, k2, h, k;
+  uint32_t* out_idx;
+  float* out_dist;
+  int vec4;
+};
+
+template <int S2, int S>
+__global__ void __launch_bounds__(SWARPS * 32) sketch_search_kernel(SketchSearchArgs a) {
+  __shared__ uint64_t s_q[SWARPS][SK_MAX_WORDS];
+  __shared__ uint32_t s_c2[SWARPS][32 * S2];
+  __shared__ uint32_t s_id[SWARPS][32];
+  __shared__ uint32_t s_row[SWARPS][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t qi = (int64_t)blockIdx.x * SWARPS + wib;
+  if (qi >= a.nq) return;
+  if (lane < a.words) s_q[wib][lane] = a.qsk[(size_t)qi * a.words + lane];
+  __syncwarp();
+
+  // Hamming stage
+  WarpList<S2> l2;
+  l2.init();
+  for (int t = 0; t < a.T; ++t) {
+    const int64_t pos = a.pos[(size_t)t * a.nq + qi];
+    const uint32_t* sig = a.sigma + (size_t)t * a.n;
+    const int64_t c0 = pos - a.w > 0 ? pos - a.w : 0;
+    const int64_t c1 = pos + a.w < a.n ? pos + a.w : a.n;
+    for (int64_t cb = c0; cb < c1; cb += 32) {
+      const int64_t c = cb + lane;
+      uint32_t pid = c < c1 ? __ldg(sig + c) : 0xffffffffu;
+      float hd = INFINITY;
+      if (pid != 0xffffffffu) {
+        const uint64_t* row = a.sk + (size_t)pid * a.words;
+        int hm = 0;
+        for (int u = 0; u < a.words; ++u) hm += __popcll(s_q[wib][u] ^ __ldg(row + u));
+        hd = (float)hm;
+      }
+      warp_sort(hd, pid, lane);
+      for (int u = 0; u < 32; ++u) {
+        const float cd = __shfl_sync(FULL, hd, u);
+        const uint32_t ci = __shfl_sync(FULL, pid, u);
+        if (ci == 0xffffffffu) break;
+        float kd;
+        uint32_t ki;
+        l2.last(a.k2, kd, ki);
+        if (!lessp(cd, ci, kd, ki)) break;
+        l2.insert(cd, ci, a.k2, lane);
+      }
+    }
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < S2; ++s2) s_c2[wib][32 * s2 + lane] = 32 * s2 + lane < a.k2 ? l2.iv[s2] : 0xffffffffu;
+  __syncwarp();
+
+  // expansion and final stage
+  const float* qv = a.q + (size_t)qi * a.d;
+  WarpList<S> list;
+  list.init();
+  const int span = 2 * a.h + 1;
+  const int64_t E = (int64_t)a.k2 * span;
+  for (int64_t eb = 0; eb < E; eb += 32) {
+    const int64_t e = eb + lane;
+    uint32_t pid = 0xffffffffu, row = 0;
+    if (e < E) {
+      const int u = (int)(e / span), o = (int)(e % span) - a.h;
+      const uint32_t c = s_c2[wib][u];
+      if (c != 0xffffffffu) {
+        const int64_t p = (int64_t)__ldg(a.posm + c) + o;
+        if (p >= 0 && p < a.n) {
+          row = (uint32_t)p;
+          pid = __ldg(a.sig0 + p);
+        }
+      }
+    }
+    float dist;
+    if (a.vec4) {
+      s_id[wib][lane] = pid;
+      s_row[wib][lane] = row;
+      __syncwarp();
+      float part[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) part[u] = 0.f;
+      for (int m = 4 * lane; m < a.d; m += 128) {
+        const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + m));
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += 16) {
+          float4 xb[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            // an empty entry reads master row 0; its result is discarded
+            xb[u] = __ldg(reinterpret_cast<const float4*>(a.xm + (size_t)s_row[wib][u0 + u] * a.d + m));
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            float ee = qa.x - xb[u].x;
+            float acc = fmaf(ee, ee, part[u0 + u]);
+            ee = qa.y - xb[u].y;
+            acc = fmaf(ee, ee, acc);
+            ee = qa.z - xb[u].z;
+            acc = fmaf(ee, ee, acc);
+            ee = qa.w - xb[u].w;
+            part[u0 + u] = fmaf(ee, ee, acc);
+          }
+        }
+      }
+      dist = warp_transpose_sum(part, lane);
+      __syncwarp();
+    } else {
+      dist = 0.f;
+      if (pid != 0xffffffffu) {
+        const float* xv = a.xm + (size_t)row * a.d;
+        for (int j = 0; j < a.d; ++j) {
+          const float ee = __ldg(qv + j) - __ldg(xv + j);
+          dist = fmaf(ee, ee, dist);
+        }
+      }
+    }
+    if (pid == 0xffffffffu) dist = INFINITY;
+    warp_sort(dist, pid, lane);
+    for (int u = 0; u < 32; ++u) {
+      const float cd = __shfl_sync(FULL, dist, u);
+      const uint32_t ci = __shfl_sync(FULL, pid, u);
+      if (ci == 0xffffffffu) break;
+      float kd;
+      uint32_t ki;
+      list.last(a.k, kd, ki);
+      if (!lessp(cd, ci, kd, ki)) break;
+      list.insert(cd, ci, a.k, lane);
+    }
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < S; ++s2) {
+    const int e = 32 * s2 + lane;
+    if (e < a.k) {
+      a.out_idx[(size_t)qi * a.k + e] = list.iv[s2];
+      a.out_dist[(size_t)qi * a.k + e] = list.dv[s2];
+    }
+  }
+}
+
+// Master-ordered copy of the points and the inverse of the master order.
+__global__ void master_layout_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sig0,
+                                     float* __restrict__ xm, uint32_t* __restrict__ posm) {
+  const int64_t total = n * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e / d;
+    const int j = (int)(e - p * d);
+    const uint32_t id = __ldg(sig0 + p);
+    xm[e] = __ldg(x + (size_t)id * d + j);
+    if (j == 0) posm[id] = (uint32_t)p;
+  }
+}
+
+template <int S2, int S>
+int launch_ss(const SketchSearchArgs& a, cudaStream_t s) {
+  sketch_search_kernel<S2, S><<<hf_blocks(a.nq, SWARPS), SWARPS * 32, 0, s>>>(a);
+  hf_after_launch("sketch_search_kernel", s);
+  return HF_OK;
+}
+
+template <int S>
+int launch_ss_k2(const SketchSearchArgs& a, cudaStream_t s) {
+  if (a.k2 <= 32) return launch_ss<1, S>(a, s);
+  if (a.k2 <= 64) return launch_ss<2, S>(a, s);
+  if (a.k2 <= 128) return launch_ss<4, S>(a, s);
+  if (a.k2 <= 256) return launch_ss<8, S>(a, s);
+  if (a.k2 <= 512) return launch_ss<16, S>(a, s);
+  return launch_ss<32, S>(a, s);
+}
+
+}  // namespace
+
+void launch_master_layout(const float* x, int64_t n, int d, const uint32_t* sig0, float* xm, uint32_t* posm,
+                          cudaStream_t s) {
+  master_layout_kernel<<<hf_blocks(n * d, 256, 152 * 16), 256, 0, s>>>(x, n, d, sig0, xm, posm);
+  hf_after_launch("master_layout_kernel", s);
+}
+
+int launch_sketch_search(const hf_forest* f, const float* q, int64_t nq, const int64_t* pos, const uint64_t* qsk,
+                         int k, int w, int k2, int h, uint32_t* out_idx, float* out_dist, cudaStream_t s) {
+  if (k < 1 || k > 64 || k2 < 1 || k2 > HF_MAX_K2 || h < 0 || !f->sketch || !f->xm || !f->posm) return HF_EINVAL;
+  const int words = f->sketch_bits / 64;
+  if (words < 1 || words > SK_MAX_WORDS) return HF_EINVAL;
+  SketchSearchArgs a;
+  a.q = q;
+  a.nq = nq;
+  a.d = f->d;
+  a.xm = f->xm;
+  a.sig0 = f->sigma;
+  a.posm = f->posm;
+  a.sigma = f->sigma;
+  a.pos = pos;
+  a.sk = f->sketch;
+  a.qsk = qsk;
+  a.words = words;
+  a.n = f->n;
+  a.T = f->T;
+  a.w = w;
+  a.k2 = k2;
+  a.h = h;
+  a.k = k;
+  a.out_idx = out_idx;
+  a.out_dist = out_dist;
+  a.vec4 = (f->d % 4 == 0) && ((reinterpret_cast<uintptr_t>(f->xm) & 15) == 0) &&
+           ((reinterpret_cast<uintptr_t>(q) & 15) == 0);
+  return k <= 32 ? launch_ss_k2<1>(a, s) : launch_ss_k2<2>(a, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -504,6 +749,7 @@ bool on_device(const void* p) {
 extern "C" int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
                                 int32_t* out_idx, float* out_dist, void* stream) {
   if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (f->mode == 3) return HF_ENOTIMPL;  // the sketch form needs per-call scratch
   if (nq == 0) return HF_OK;
   if (!queries || !out_idx || !out_dist) return HF_EINVAL;
   if ((uint64_t)nq * (uint64_t)f->d > (uint64_t)HF_STATIC_QUERY_BYTES) return HF_EINVAL;

@@ -85,6 +85,12 @@ def test_sketch_rejects_bad_lengths(hf):
     with pytest.raises(hf.HFError):  # sketch form before the sketches exist
         G.set_option("mode", 3)
         G.knn_graph(5, 8)
+    G.set_sketch(S.sketch_projection(64, 16))
+    G.set_option("sketch_k2", 100)
+    with pytest.raises(hf.HFError):  # the graph's band lists hold at most 64
+        G.knn_graph(5, 8)
+    with pytest.raises(hf.HFError):
+        G.set_option("sketch_k2", 1025)
     G.close()
 
 
@@ -170,4 +176,83 @@ def test_sketch_k2_all_candidates_equals_graph(hf):
     gi, gd = G.knn_graph(k, w)
     oi, od = O.knn_graph(F, k, w)
     check_lists(x, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, owners=np.arange(n), cand=O.candidate_sets(F, w))
+    G.close()
+
+
+# ---------------------------------------------------------------- search side
+@pytest.mark.parametrize("n,d,T,w,k,k2,h,nq", [
+    (5003, 64, 4, 20, 10, 60, 2, 300),      # Table 1's h; two-slot Hamming list
+    (4001, 40, 3, 64, 30, 300, 2, 200),     # k = 30, k2 = 300 (16-slot list)
+    (3001, 24, 2, 300, 15, 1000, 1, 100),   # the largest k2
+    (2000, 36, 3, 16, 5, 7, 0, 150),        # no expansion, k2 < 32
+    (70, 8, 2, 30, 40, 50, 3, 20),          # k > 32, windows wider than the set
+])
+def test_sketch_search_exact_on_integer_points(hf, n, d, T, w, k, k2, h, nq):
+    x = S.small_integer_points(n, d, seed=7)
+    q = S.small_integer_points(nq, d, seed=8)
+    R = S.small_integer_projection(128, d, seed=9)
+    G = hf.build(cuda(x), T=T, bits=8, seed=10)
+    F = O.Forest(x, T=T, bits=8, seed=10)
+    G.set_sketch(cuda(R))
+    G.set_option("mode", 3)
+    G.set_option("sketch_k2", k2)
+    G.set_option("expand_h", h)
+    gi, gd = G.search(cuda(q), k, w)
+    oi, od = OS.search_sketch(F, q, k, w, OS.sketches(x, R), OS.sketches(q, R), k2, h)
+    assert np.array_equal(gi.cpu().numpy().astype(np.int64), oi)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+    # a second call reuses the master layout
+    gi2, _ = G.search(cuda(q), k, w)
+    assert np.array_equal(gi2.cpu().numpy(), gi.cpu().numpy())
+    G.close()
+
+
+def test_sketch_search_gaussian_workload_shape(hf):
+    """Table 1's k, k2 and h on mixture data at d = 384; rows whose query and
+    candidates all carry the oracle's sketches are compared with the oracle."""
+    n, d, T, w, k, k2, h, nq, bits = 20000, 384, 8, 50, 30, 300, 2, 400, 384
+    x = S.gaussian_mixture(n, d, n_components=100, seed=12)
+    q = S.mixture_queries(nq, d, n_components=100, data_seed=12, seed=13)
+    R = S.sketch_projection(bits, d, seed=14)
+    G = hf.build(cuda(x), T=T, bits=8, seed=15)
+    F = O.Forest(x, T=T, bits=8, seed=15)
+    G.set_sketch(cuda(R))
+    G.set_option("mode", 3)
+    G.set_option("sketch_k2", k2)
+    G.set_option("expand_h", h)
+    gi, gd = G.search(cuda(q), k, w)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    sk, qsk = OS.sketches(x, R), OS.sketches(q, R)
+    flipped = unpack(G.sketches(), bits) != unpack(sk, bits)
+    assert not (flipped & ~ambiguous_bits(x, R)).any()
+    moved = flipped.any(axis=1)
+    # the query sketches are not exported: a query within the bound of a
+    # decision anywhere is compared loosely
+    qmoved = ambiguous_bits(q, R).any(axis=1)
+    oi, od = OS.search_sketch(F, q, k, w, sk, qsk, k2, h)
+    cand = O.search_candidates(F, q, w)
+    touched = qmoved | np.array([moved[c[c >= 0]].any() for c in cand])
+    strict = np.flatnonzero(~touched)
+    assert strict.size >= nq // 2, f"only {strict.size} strict rows"
+    check_lists(x, gi[strict], gd[strict], oi[strict], od[strict], queries=q[strict], min_equal=0.99)
+    same = np.mean([len(set(a[a >= 0]) & set(b[b >= 0])) / max(1, (b >= 0).sum()) for a, b in zip(gi, oi)])
+    assert same >= 0.99
+    G.close()
+
+
+def test_sketch_search_without_filters_is_the_search(hf):
+    n, d, T, w, k = 4000, 32, 3, 10, 8
+    x = S.unit_gaussian(n, d, seed=16)
+    q = S.unit_gaussian(100, d, seed=17)
+    G = hf.build(cuda(x), T=T, bits=8, seed=18)
+    F = O.Forest(x, T=T, bits=8, seed=18)
+    G.set_sketch(cuda(S.sketch_projection(64, d, seed=19)))
+    G.set_option("mode", 3)
+    G.set_option("sketch_k2", 2 * w * T)
+    G.set_option("expand_h", 0)
+    gi, gd = G.search(cuda(q), k, w)
+    oi, od = O.search(F, q, k, w)
+    check_lists(x, gi.cpu().numpy(), gd.cpu().numpy(), oi, od, queries=q)
+    with pytest.raises(hf.HFError):  # no scratch-free sketch form
+        G.search_static(cuda(q), k, w)
     G.close()
