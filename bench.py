@@ -85,6 +85,16 @@ def args():
     p.add_argument("--label-sample", type=int, default=200_000, help="points of the label sample")
     p.add_argument("--label-forests", type=int, default=5, help="forests (seeds) over the label sample")
     p.add_argument("--train-steps", type=int, default=3000)
+    p.add_argument("--no-sketch", action="store_true", help="skip the sketch-form comparison")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched form (64 independent sets)")
+    p.add_argument("--batched-sets", type=int, default=64)
+    p.add_argument("--batched-recall", type=float, default=0.8, help="autotuner recall target per d group")
+    p.add_argument("--batched-steps", type=int, default=3)
+    p.add_argument("--sketch-bits", type=int, default=384)
+    p.add_argument("--sketch-graph", default="80,48,60",
+                   help="T,w,k2 of the sketch-form graph (the paper's first Table 2 row: 80 sorts, k1 = 96, k2 = 60)")
+    p.add_argument("--sketch-search", default="128,300,2",
+                   help="w,k2,h of the sketch-form search over the main forest")
     p.add_argument("--recall-sweep", default="",
                    help="comma-separated T list x w list, e.g. '8,16,32,64,128,256:16,32,64,128,256': "
                         "print the plain method's recall@k over that (T, w) grid and exit")
@@ -309,6 +319,12 @@ def run_ours(a):
     learned = None
     if not a.no_learned and a.mode != "plain":
         learned = learned_form(a, hf, xd, qd, rows, ex, si, sd, stream, dev)
+    sketch = None
+    if not a.no_sketch:
+        sketch = sketch_form(a, hf, xd, qd, rows, ex, exq, qs, dev)
+    batched = None
+    if not a.no_batched and rank == 0:
+        batched = batched_form(a, hf, dev)
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x).pin_memory()
@@ -370,6 +386,8 @@ def run_ours(a):
             "roofline": roof,
             "plain_f32": plain,
             "learned": learned,
+            "sketch": sketch,
+            "batched": batched,
             "e2e": {"value": job_value(ws, n, e2e_step), "unit": "points/s",
                     "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
@@ -689,6 +707,196 @@ def learned_form(a, hf, xd, qd, rows, ex, si, sd, stream, dev):
             "train": {"labels": ns * len(ys), "label_sample": ns, "forests": len(ys), "steps": a.train_steps,
                       "batch": 1024, "final_loss": loss, "labels_s": labels_s, "train_s": train_s},
             "model": "MLP d-256-256-2, GELU, BF16 weights/activations, FP32 accumulation (tcgen05), Adam"}
+
+
+def sketch_form(a, hf, xd, qd, rows, ex, exq, qs, dev):
+    """The paper's second stage on this workload, outside the timed region:
+    the graph in the sketch form against the BF16 Gram form at the same
+    (T, w) budget, and the search in the sketch form against the plain search
+    at the main window, each one timed step with its recall@k."""
+    import torch
+    import synthdata as S
+
+    n, d, k = a.n, a.d, a.k
+    Tg, wg, k2g = (int(v) for v in a.sketch_graph.split(","))
+    ws, k2s, hs = (int(v) for v in a.sketch_search.split(","))
+    R = torch.from_numpy(S.sketch_projection(a.sketch_bits, d)).to(dev)
+    gi = torch.empty((n, k), dtype=torch.int32, device=dev)
+    gd = torch.empty((n, k), dtype=torch.float32, device=dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    out = {"bits": a.sketch_bits, "projection": "i.i.d. N(0, 1) rows (sign random projection)"}
+    graph = {"T": Tg, "w": wg, "k2": k2g}
+    for form, mode in (("sketch", 3), ("tensor", 1)):
+        G = hf.build(xd, T=Tg, bits=a.bits, seed=3)
+        torch.cuda.synchronize()
+        e0 = ev()
+        if mode == 3:
+            G.set_sketch(R)
+            G.set_option("sketch_k2", k2g)
+        G.set_option("mode", mode)
+        G.knn_graph(k, wg, gi, gd)
+        e1 = ev()
+        torch.cuda.synchronize()
+        ms = G.timings()
+        graph[form] = {"ms_per_step": e0.elapsed_time(e1), "build_ms": ms["keys"] + ms["sort"] + ms["tie_fixup"],
+                       "window_ms": ms["window_merge"], "rerank_ms": ms["rerank"],
+                       "recall_at_k": recall(gi.cpu().numpy()[rows], ex)}
+        graph[form]["value"] = n / (graph[form]["ms_per_step"] * 1e-3)
+        G.close()
+    out["graph"] = graph
+    G = hf.build(xd, T=a.T, bits=a.bits, seed=3)
+    G.set_sketch(R)
+    search = {"T": a.T, "k": k, "queries": a.nq}
+    for form, mode, w in (("sketch", 3, ws), ("plain", 0, a.search_w)):
+        G.set_option("mode", mode)
+        G.set_option("sketch_k2", k2s)
+        G.set_option("expand_h", hs)
+        G.search(qd, k, w)  # the first sketch search builds the master layout
+        torch.cuda.synchronize()
+        e0 = ev()
+        si, _ = G.search(qd, k, w)
+        e1 = ev()
+        torch.cuda.synchronize()
+        search[form] = {"w": w, "ms": e0.elapsed_time(e1), "queries_per_s": a.nq / (e0.elapsed_time(e1) * 1e-3),
+                        "recall_at_k": recall(si[:qs].cpu().numpy(), exq)}
+        if mode == 3:
+            search[form].update({"k2": k2s, "h": hs})
+    out["search"] = search
+    G.close()
+    return out
+
+
+def batched_form(a, hf, dev):
+    """The batched workload, outside the main timed region: independent sets
+    (sizes log-uniform in [1,000, 200,000], d from {64, 128, 384, 768}, 100-
+    component mixtures, T = 16, b = 8, k = 10), stacked per dimension into one
+    segmented forest each. The autotuner picks each group's window and block
+    size for the recall target on a sample; a step is the segmented builds
+    plus one CUDA-graph replay of all groups' graphs. Beside it, the same sets
+    one at a time (hf_build + hf_knn_graph per set, same windows)."""
+    import torch
+    import synthdata as S
+
+    T, k = 16, 10
+    sets = S.batched_sets(a.batched_sets)
+    dims = sorted({x.shape[1] for x in sets})
+    groups = []
+    for d in dims:
+        idx = [i for i, x in enumerate(sets) if x.shape[1] == d]
+        off = np.zeros(len(idx) + 1, np.int64)
+        off[1:] = np.cumsum([sets[i].shape[0] for i in idx])
+        X = torch.from_numpy(np.concatenate([sets[i] for i in idx])).to(dev)
+        groups.append({"d": d, "idx": idx, "off": off, "X": X})
+    n_total = int(sum(x.shape[0] for x in sets))
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    # autotune per group (one build each)
+    for g in groups:
+        G = hf.build_segmented(g["X"], g["off"], T=T, bits=a.bits, seed=3)
+        g["tune"] = G.autotune(k, a.batched_recall, sample=1024, w_max=704, forms=7)
+        G.close()
+    for g in groups:
+        n = g["X"].shape[0]
+        g["oi"] = torch.empty((n, k), dtype=torch.int32, device=dev)
+        g["od"] = torch.empty((n, k), dtype=torch.float32, device=dev)
+
+    def ev(st):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        return e
+
+    def batched_step(capture_graph):
+        with torch.cuda.stream(side):
+            forests = [hf.build_segmented(g["X"], g["off"], T=T, bits=a.bits, seed=3) for g in groups]
+            for G, g in zip(forests, groups):
+                G.set_option("mode", g["tune"]["form"])
+                G.graph_plan(k, g["tune"]["w"], g["tune"]["threads"], side.cuda_stream)
+            graph = None
+            if capture_graph:
+                graph = hf.CudaGraph(side.cuda_stream)
+                with graph:
+                    for G, g in zip(forests, groups):
+                        G.knn_graph_enqueue(g["oi"], g["od"], side.cuda_stream)
+            return forests, graph
+
+    # warm-up (also the capture's first use)
+    forests, graph = batched_step(True)
+    graph.launch()
+    for G in forests:
+        G.status(side.cuda_stream)
+    l_cap = None
+    ms, build_ms, replay_ms = [], [], []
+    for _ in range(a.batched_steps):
+        for G in forests:
+            G.close()
+        graph.close()
+        torch.cuda.synchronize(dev)
+        l0 = hf.launch_count()
+        e0 = ev(side)
+        forests, graph = batched_step(True)
+        e1 = ev(side)
+        l1 = hf.launch_count()
+        graph.launch()
+        e2 = ev(side)
+        for G in forests:
+            G.status(side.cuda_stream)
+        ms.append(e0.elapsed_time(e2))
+        build_ms.append(e0.elapsed_time(e1))
+        replay_ms.append(e1.elapsed_time(e2))
+        l_cap = l1 - l0
+    step_ms = statistics.mean(ms)
+    # per-set recall on sampled rows (exact rows within each set)
+    per_set = [None] * len(sets)
+    for G, g in zip(forests, groups):
+        gi = g["oi"].cpu().numpy()
+        for j, i in enumerate(g["idx"]):
+            a0, a1 = int(g["off"][j]), int(g["off"][j + 1])
+            rows = np.unique(np.linspace(a0, a1 - 1, num=min(32, a1 - a0)).astype(np.int64))
+            ei, _ = G.exact_knn_rows(rows, k)
+            hit = sum(len(set(x[x >= 0]) & set(y[y >= 0])) for x, y in zip(gi[rows], ei))
+            per_set[i] = {"n": a1 - a0, "d": g["d"], "recall_at_k": hit / max(1, int((ei >= 0).sum()))}
+    for G in forests:
+        G.close()
+    graph.close()
+    # the same sets one at a time
+    wmap = {g["d"]: g["tune"]["w"] for g in groups}
+    fmap = {g["d"]: g["tune"]["form"] for g in groups}
+    xs = [torch.from_numpy(x).to(dev) for x in sets]
+    one_ms = []
+    l0 = hf.launch_count()
+    for i, x in enumerate(xs):
+        torch.cuda.synchronize(dev)
+        e0 = ev(torch.cuda.current_stream(dev))
+        G = hf.build(x, T=T, bits=a.bits, seed=3)
+        G.set_option("mode", fmap[x.shape[1]])
+        G.knn_graph(k, wmap[x.shape[1]])
+        e1 = ev(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        one_ms.append(e0.elapsed_time(e1))
+        per_set[i]["one_at_a_time_ms"] = one_ms[-1]
+        per_set[i]["one_at_a_time_points_per_s"] = x.shape[0] / (one_ms[-1] * 1e-3)
+        G.close()
+    l_one = hf.launch_count() - l0
+    loop_ms = float(sum(one_ms))
+    return {
+        "workload": f"{len(sets)} independent sets, sizes log-uniform [1000, 200000], d in {{64,128,384,768}}, "
+                    f"100-component mixtures, T={T}, b={a.bits}, k={k}",
+        "sets": len(sets), "points": n_total,
+        "groups": [{"d": g["d"], "sets": len(g["idx"]), "points": int(g["X"].shape[0]), **g["tune"]} for g in groups],
+        "ms_per_step": step_ms, "build_ms": statistics.mean(build_ms), "graph_replay_ms": statistics.mean(replay_ms),
+        "value": n_total / (step_ms * 1e-3), "unit": "points/s",
+        "launches_per_step": int(l_cap), "one_at_a_time": {"ms": loop_ms, "value": n_total / (loop_ms * 1e-3),
+                                                           "launches": int(l_one)},
+        "speedup_vs_one_at_a_time": loop_ms / step_ms,
+        "recall_target": a.batched_recall,
+        "recall_at_k_mean": float(np.mean([p["recall_at_k"] for p in per_set])),
+        "per_set": per_set,
+    }
 
 
 def recall_sweep(a):

@@ -175,6 +175,79 @@ int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t
 int hf_search_static(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w,
                      int32_t* out_idx, float* out_dist, void* stream);
 
+/* ---- batched form: many independent point sets -----------------------------
+ * Many small independent problems (point sets of uneven size) are built and
+ * graphed together so that every kernel launch covers all of them: the paper
+ * treats one dataset at a time; this is an interface and scheduling extension
+ * with the same per-set results.
+ *
+ * hf_build_segmented -- one forest over nsets independent sets stacked in one
+ * row-major matrix: rows offsets[s] .. offsets[s+1]-1 form set s (offsets: host,
+ * nsets + 1 values, offsets[0] = 0, every set at least 2 rows, nsets <=
+ * HF_MAX_SETS). Each set is quantized with its own per-axis range; all sets
+ * share the T per-tree permutations and reflections of `seed`; every order
+ * lists set 0's points first (in their own Hilbert order), then set 1's, ...
+ * hf_knn_graph then gives, for every row, exactly the lists hf_build +
+ * hf_knn_graph give on that set alone (plain and sketch forms), with row
+ * indices of the stacked matrix (subtract offsets[s]). Tensor forms, the
+ * budgeted graph and search return HF_ENOTIMPL on a segmented forest.
+ */
+#define HF_MAX_SETS 256
+int hf_build_segmented(const float* points, const int64_t* offsets, int32_t nsets, int32_t d, int32_t T,
+                       int32_t bits, uint64_t seed, const char* options, void* stream, hf_forest** out);
+
+/*
+ * Enqueue-only graph, for CUDA-graph capture (plain or Gram form: the forest's
+ * mode 0, 1 or 2 when hf_graph_plan runs; a window the form cannot run is
+ * HF_ENOTIMPL, never a change of form). hf_graph_plan keeps per-point lists
+ * (and, for the Gram forms, the operand copies) in the forest for (k, w) and
+ * the plain window kernel's block size `threads` (0: chosen per band, else
+ * 256 or 512). hf_knn_graph_enqueue then enqueues the whole graph on
+ * `stream` into DEVICE outputs (n x k) without allocating or synchronising,
+ * so it can be captured; errors surface through hf_status, which synchronises
+ * `stream` and reads and clears the device error word.
+ */
+int hf_graph_plan(hf_forest* f, int32_t k, int32_t w, int32_t threads, void* stream);
+int hf_knn_graph_enqueue(hf_forest* f, int32_t* out_idx, float* out_dist, void* stream);
+int hf_status(hf_forest* f, void* stream);
+
+/*
+ * CUDA graphs of enqueue-only work: hf_capture_begin starts a (relaxed)
+ * capture on `stream` (not the legacy default stream), hf_capture_end ends it
+ * and instantiates the graph into *exec; hf_graph_launch replays it on
+ * `stream`; hf_graph_destroy frees it.
+ */
+int hf_capture_begin(void* stream);
+int hf_capture_end(void* stream, void** exec);
+int hf_graph_launch(void* exec, void* stream);
+int hf_graph_destroy(void* exec);
+
+/*
+ * hf_exact_knn_rows -- exact k nearest neighbours (float32 exact differences,
+ * ties by index, the row itself excluded) of the given rows (host int64) among
+ * the points of their own set; out_idx / out_dist nrows x k, host or device.
+ * The ground truth of recall estimates (autotuner, tests).
+ */
+int hf_exact_knn_rows(hf_forest* f, const int64_t* rows, int32_t nrows, int32_t k, int32_t* out_idx,
+                      float* out_dist, void* stream);
+
+/*
+ * hf_autotune -- picks the graph plan for (k, target recall): for each form
+ * in the mask `forms` (bit 0 plain float32, bit 1 BF16 Gram, bit 2 FP8 Gram),
+ * the smallest window w of a fixed ladder (2 .. w_max, within the form's
+ * limits) whose graph reaches target_recall on `sample` evenly spread rows
+ * (recall against hf_exact_knn_rows; it grows with w because the candidate
+ * sets grow), found by bisection, and at that w the faster block size of
+ * the plain window kernel (256 or 512 threads; the Gram kernel is
+ * persistent); then the fastest form that reaches the target (CUDA-event
+ * time of the whole graph), else the one with the highest recall. Leaves
+ * that form (hf_set_option mode) and plan (hf_graph_plan) in the forest and
+ * reports them with the sample recall and the graph's time.
+ */
+int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, int32_t w_max, int32_t forms,
+                int32_t* out_form, int32_t* out_w, int32_t* out_threads, double* out_recall, float* out_ms,
+                void* stream);
+
 /* ---- second stage: binary sketches ----------------------------------------
  * The paper filters the forest's candidates by the Hamming distance of 384-bit
  * sketches before the final vector distances (Section 3 index structure;

@@ -34,6 +34,8 @@ SYMBOLS = [
     "hf_budget_labels", "hf_knn_graph_budget", "hf_mlp_create", "hf_mlp_free", "hf_mlp_param_count",
     "hf_mlp_get_params", "hf_mlp_set_params", "hf_mlp_predict", "hf_mlp_grads", "hf_mlp_train",
     "hf_set_sketch", "hf_debug_sketch",
+    "hf_build_segmented", "hf_graph_plan", "hf_knn_graph_enqueue", "hf_status", "hf_capture_begin",
+    "hf_capture_end", "hf_graph_launch", "hf_graph_destroy", "hf_exact_knn_rows", "hf_autotune",
 ]
 
 _lib = None
@@ -86,6 +88,16 @@ def lib() -> ctypes.CDLL:
         "hf_mlp_train": [vp, vp, vp, i64, i32, i32, ctypes.c_float, vp, vp],
         "hf_set_sketch": [vp, vp, i32, vp],
         "hf_debug_sketch": [vp, vp, vp],
+        "hf_build_segmented": [vp, vp, i32, i32, i32, i32, u64, ctypes.c_char_p, vp, pp],
+        "hf_graph_plan": [vp, i32, i32, i32, vp],
+        "hf_knn_graph_enqueue": [vp, vp, vp, vp],
+        "hf_status": [vp, vp],
+        "hf_capture_begin": [vp],
+        "hf_capture_end": [vp, pp],
+        "hf_graph_launch": [vp, vp],
+        "hf_graph_destroy": [vp],
+        "hf_exact_knn_rows": [vp, vp, i32, i32, vp, vp, vp],
+        "hf_autotune": [vp, i32, ctypes.c_double, i32, i32, i32, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -169,14 +181,22 @@ def _empty_like_input(ref, shape, dtype):
 class Forest:
     """A built Hilbert forest (hf_build). Holds the library handle."""
 
-    def __init__(self, points, T: int, bits: int = 8, seed: int = 3, options: str | None = None):
+    def __init__(self, points, T: int, bits: int = 8, seed: int = 3, options: str | None = None, offsets=None):
         n, d = points.shape
         self.n, self.d, self.T, self.bits = int(n), int(d), int(T), int(bits)
         self._points = points  # the library borrows device memory: keep it alive
         p, _ = _ptr(points)
         h = ctypes.c_void_p()
         st = _stream(points)
-        if options is None:
+        self.offsets = None
+        if offsets is not None:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            if off.ndim != 1 or off[0] != 0 or off[-1] != n:
+                raise ValueError("offsets must start at 0 and end at the row count")
+            self.offsets = off
+            rc = lib().hf_build_segmented(p, off.ctypes.data, len(off) - 1, d, T, bits, seed,
+                                          options.encode() if options else None, st, ctypes.byref(h))
+        elif options is None:
             rc = lib().hf_build(p, n, d, T, bits, seed, st, ctypes.byref(h))
         else:
             rc = lib().hf_build_opts(p, n, d, T, bits, seed, options.encode(), st, ctypes.byref(h))
@@ -278,6 +298,40 @@ class Forest:
                                       op, cp, _stream(knn)), "hf_budget_labels")
         return out_targets, out_cell
 
+    # ---- enqueue-only graph, autotuner, exact rows
+    def graph_plan(self, k: int, w: int, threads: int = 0, stream=None):
+        _check(lib().hf_graph_plan(self._h, k, w, threads, stream), "hf_graph_plan")
+        self.plan_k = int(k)
+
+    def knn_graph_enqueue(self, out_idx, out_dist, stream=None):
+        """Enqueues the planned graph into CUDA tensors (n x k); no sync."""
+        ip, _a = _ptr(out_idx)
+        dp, _b = _ptr(out_dist)
+        _check(lib().hf_knn_graph_enqueue(self._h, ip, dp, stream if stream is not None else _stream(out_idx)),
+               "hf_knn_graph_enqueue")
+
+    def status(self, stream=None):
+        _check(lib().hf_status(self._h, stream), "hf_status")
+
+    def exact_knn_rows(self, rows, k: int):
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        oi = np.empty((rows.size, k), np.int32)
+        od = np.empty((rows.size, k), np.float32)
+        _check(lib().hf_exact_knn_rows(self._h, rows.ctypes.data, rows.size, k, oi.ctypes.data, od.ctypes.data,
+                                       _stream(self._points)), "hf_exact_knn_rows")
+        return oi, od
+
+    def autotune(self, k: int, target_recall: float, sample: int = 512, w_max: int = 512, forms: int = 1):
+        """hf_autotune over the forms in the mask (1 plain, 2 BF16 Gram, 4 FP8
+        Gram); returns the chosen form, w, block size, sample recall and ms."""
+        fm, w, nt = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        rec, ms = ctypes.c_double(), ctypes.c_float()
+        _check(lib().hf_autotune(self._h, k, target_recall, sample, w_max, forms, ctypes.byref(fm), ctypes.byref(w),
+                                 ctypes.byref(nt), ctypes.byref(rec), ctypes.byref(ms), _stream(self._points)),
+               "hf_autotune")
+        self.plan_k = int(k)
+        return {"form": fm.value, "w": w.value, "threads": nt.value, "recall": rec.value, "ms": ms.value}
+
     def set_sketch(self, R):
         """hf_set_sketch: sketches of all points from the projection R
         (bits x d float32, CUDA tensor or numpy)."""
@@ -334,6 +388,48 @@ class Forest:
 
 def build(points, T: int, bits: int = 8, seed: int = 3, options: str | None = None) -> Forest:
     return Forest(points, T, bits, seed, options)
+
+
+def build_segmented(points, offsets, T: int, bits: int = 8, seed: int = 3, options: str | None = None) -> Forest:
+    """hf_build_segmented: rows offsets[s] .. offsets[s+1]-1 of `points` form
+    independent set s."""
+    return Forest(points, T, bits, seed, options, offsets=offsets)
+
+
+class CudaGraph:
+    """A CUDA graph of enqueue-only library work, captured on a side stream
+    (hf_capture_begin / hf_capture_end) and replayed with launch()."""
+
+    def __init__(self, stream_handle: int):
+        self.stream = stream_handle
+        self._exec = None
+
+    def __enter__(self):
+        _check(lib().hf_capture_begin(self.stream), "hf_capture_begin")
+        return self
+
+    def __exit__(self, et, ev, tb):
+        ex = ctypes.c_void_p()
+        rc = lib().hf_capture_end(self.stream, ctypes.byref(ex))
+        if et is None:
+            _check(rc, "hf_capture_end")
+            self._exec = ex
+        return False
+
+    def launch(self, stream_handle: int | None = None):
+        _check(lib().hf_graph_launch(self._exec, self.stream if stream_handle is None else stream_handle),
+               "hf_graph_launch")
+
+    def close(self):
+        if self._exec is not None:
+            lib().hf_graph_destroy(self._exec)
+            self._exec = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mlp:

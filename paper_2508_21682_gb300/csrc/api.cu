@@ -160,6 +160,12 @@ void destroy(hf_forest* f, cudaStream_t s) {
   dfree(f->sketch_r, s);
   dfree(f->xm, s);
   dfree(f->posm, s);
+  dfree(f->seg_off, s);
+  dfree(f->seg, s);
+  dfree(f->plan_li, s);
+  dfree(f->plan_ld, s);
+  dfree(f->plan_xs, s);
+  dfree(f->plan_ms, s);
   delete f;
 }
 
@@ -250,7 +256,9 @@ void hf_after_launch(const char* what, cudaStream_t s) {
   if (!on) return;
   // peek: the error stays set for the entry point's final check
   cudaError_t e = cudaPeekAtLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (e == cudaSuccess && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+    e = cudaStreamSynchronize(s);  // no synchronisation while a graph is being captured
   fprintf(stderr, "[hf] %s: %s\n", what, cudaGetErrorString(e));
   fflush(stderr);
 }
@@ -296,8 +304,8 @@ int hf_build(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits,
   return hf_build_opts(points, n, d, T, bits, seed, nullptr, stream, out);
 }
 
-int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits, uint64_t seed,
-                  const char* options, void* stream, hf_forest** out) {
+static int build_impl(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits, uint64_t seed,
+                      const char* options, int nseg, const int64_t* seg_off, void* stream, hf_forest** out) {
   if (out) *out = nullptr;
   if (!points || !out || n < 2 || n > HF_MAX_N || d < 1 || d > HF_MAX_D || T < 1 || bits < 1 ||
       bits > HF_MAX_BITS)
@@ -305,6 +313,8 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaGetLastError();  // an earlier call's error was reported by that call
   hf_forest* f = new hf_forest();
+  f->nseg = nseg;
+  if (nseg > 1) f->seg_off_h.assign(seg_off, seg_off + nseg + 1);
   f->n = n;
   f->d = d;
   f->T = T;
@@ -362,8 +372,14 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     if (f->sort_batch_max > 0 && f->TB > f->sort_batch_max) f->TB = f->sort_batch_max;
   }
   const int TB = f->TB;
-  chk(dalloc(&f->lo, d, s));
-  chk(dalloc(&f->scale, d, s));
+  chk(dalloc(&f->lo, (size_t)nseg * d, s));
+  chk(dalloc(&f->scale, (size_t)nseg * d, s));
+  uint64_t* seg64 = nullptr;
+  if (nseg > 1) {
+    chk(dalloc(&f->seg_off, (size_t)nseg + 1, s));
+    chk(dalloc(&f->seg, (size_t)n, s));
+    chk(dalloc(&seg64, (size_t)n, s));
+  }
   chk(dalloc(&f->planes, (size_t)bits * n * W32, s));
   chk(dalloc(&f->pi, (size_t)T * d, s));
   chk(dalloc(&f->rbits, (size_t)T * W32, s));
@@ -390,10 +406,15 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   chk(dalloc_bytes(&rscratch, rbytes, s));
   if (e != cudaSuccess) {
     dfree(rscratch, s);
+    dfree(seg64, s);
     destroy(f, s);
     return map_cuda(e);
   }
   cudaMemsetAsync(f->err, 0, sizeof(int), s);
+  if (nseg > 1) {
+    cudaMemcpyAsync(f->seg_off, f->seg_off_h.data(), (size_t)(nseg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    launch_seg_of_row(f->seg_off, nseg, n, f->seg, seg64, s);
+  }
   cudaMemsetAsync(f->tie.counters, 0, (size_t)T * 4 * sizeof(uint32_t), s);
 
   // per-tree permutations and reflection masks (host, then one upload)
@@ -409,8 +430,11 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   cudaMemcpyAsync(f->rbits, hr.data(), hr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
 
   cudaEvent_t a0 = tm.mark();
-  launch_range(f->x, n, d, f->lo, f->scale, bits, f->err, rscratch, rbytes, s);
-  launch_quantize_planes(f->x, n, d, f->lo, f->scale, bits, f->planes, f->err, s);
+  if (nseg > 1)
+    launch_seg_range(f->x, d, f->seg_off, nseg, bits, f->lo, f->scale, f->err, s);
+  else
+    launch_range(f->x, n, d, f->lo, f->scale, bits, f->err, rscratch, rbytes, s);
+  launch_quantize_planes(f->x, n, d, f->lo, f->scale, bits, f->planes, f->err, s, nseg > 1 ? f->seg : nullptr);
   if (sliced) launch_plane0_slice(f->planes, n, d, f->p0t, s);
   cudaEvent_t a1 = tm.mark();
   tm.span(0, a0, a1);
@@ -437,9 +461,16 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
     for (int t = 0; t < T && rc == HF_OK; ++t) rc = tie_fixup_big(f, t, ctr[(size_t)t * 4 + 1], s);
     cudaEvent_t b1 = tm.mark();
     tm.span(3, b0, b1);
+    if (rc == HF_OK && nseg > 1) {
+      cudaEvent_t c0 = tm.mark();
+      rc = segment_pass(f, seg64, s);
+      cudaEvent_t c1 = tm.mark();
+      tm.span(2, c0, c1);
+    }
     if (rc == HF_OK) rc = finish(f, s);
   }
   dfree(rscratch, s);
+  dfree(seg64, s);
   if (rc == HF_OK) {
     tm.collect({0, 1, 2, 3});
     // keys, prefix gather and tie kernels per tree; histogram, scan and 8K
@@ -454,6 +485,21 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
   }
   *out = f;
   return HF_OK;
+}
+
+int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t bits, uint64_t seed,
+                  const char* options, void* stream, hf_forest** out) {
+  return build_impl(points, n, d, T, bits, seed, options, 1, nullptr, stream, out);
+}
+
+int hf_build_segmented(const float* points, const int64_t* offsets, int32_t nsets, int32_t d, int32_t T, int32_t bits,
+                       uint64_t seed, const char* options, void* stream, hf_forest** out) {
+  if (out) *out = nullptr;
+  if (!offsets || nsets < 1 || nsets > HF_MAX_SETS || offsets[0] != 0) return HF_EINVAL;
+  for (int g = 0; g < nsets; ++g)
+    if (offsets[g + 1] - offsets[g] < 2) return HF_EINVAL;  // every set holds two points at least
+  if (nsets == 1) return build_impl(points, offsets[1], d, T, bits, seed, options, 1, nullptr, stream, out);
+  return build_impl(points, offsets[nsets], d, T, bits, seed, options, nsets, offsets, stream, out);
 }
 
 int hf_free(hf_forest* f) {
@@ -531,6 +577,7 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   const bool sketchf = form == 3;
   if (sketchf && !f->sketch) return HF_ESTATE;            // hf_set_sketch first
   if (sketchf && f->sketch_k2 > HF_MAX_K) return HF_ENOTIMPL;  // the band lists hold at most 64
+  if (f->nseg > 1 && budget) return HF_ENOTIMPL;                 // segmented forests: uniform windows
   if (!tensor && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;  // widest window the plain band launches cover
   if (!tensor && budget) return HF_ENOTIMPL;              // per-point windows: tensor forms only
   f->timings[8] = (float)form;  // the form that runs
@@ -581,12 +628,12 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
       launch_gather_rows(f->xb, f->xmeta, form, n, f->d, sig, xs, ms, s);
       cudaEvent_t g1 = tm.mark();
       tm.span(9, g0, g1);
-      rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs, ms, s);
+      rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs, ms, s, f->seg, f->seg_off);
     } else if (sketchf) {
       rc = launch_window_hamming(reinterpret_cast<const uint32_t*>(f->sketch), n, f->sketch_bits / 32,
-                                 f->sigma + (size_t)t * n, w, kp, li, ldd, s);
+                                 f->sigma + (size_t)t * n, w, kp, li, ldd, s, f->seg, f->seg_off);
     } else
-      rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s);
+      rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s, f->seg, f->seg_off);
   }
   cudaEvent_t a1 = tm.mark();
   if (rc == HF_OK && (tensor || sketchf))
@@ -641,6 +688,299 @@ int hf_knn_graph_budget(hf_forest* f, int32_t k, const int32_t* w_pt, const int3
     return HF_EINVAL;
   if (classify(w_pt) != 1 || classify(T_pt) != 1) return HF_EINVAL;
   return knn_graph_impl(f, k, w_max, w_pt, T_pt, T_max, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+// ---- enqueue-only graph, CUDA graphs, exact rows, autotuner ---------------
+
+int hf_graph_plan(hf_forest* f, int32_t k, int32_t w, int32_t threads, void* stream) {
+  if (!f || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (threads != 0 && threads != 256 && threads != 512) return HF_EINVAL;
+  if (f->mode == 3) return HF_ENOTIMPL;
+  const int form = f->mode;  // 0 plain, 1 BF16 Gram, 2 FP8 Gram
+  if (form == 0 && w > HF_PLAIN_MAX_W) return HF_ENOTIMPL;
+  if (form != 0 && !gram_supported(f->d, w, form)) return HF_ENOTIMPL;  // no silent change of form here
+  const int slack = f->tensor_slack < 0 ? 1 : f->tensor_slack;
+  const int kp = window_list_pitch(form ? k + slack : k);
+  if (form && kp > 32) return HF_ENOTIMPL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  const int64_t n = f->n;
+  cudaError_t e = cudaSuccess;
+  if (kp != f->plan_kp || !f->plan_li) {
+    dfree(f->plan_li, s);
+    dfree(f->plan_ld, s);
+    e = dalloc(&f->plan_li, (size_t)n * kp, s);
+    if (e == cudaSuccess) e = dalloc(&f->plan_ld, (size_t)n * kp, s);
+  }
+  if (e == cudaSuccess && form && (form != f->plan_form || !f->plan_xs)) {
+    dfree(f->plan_xs, s);
+    dfree(f->plan_ms, s);
+    e = dalloc_bytes(&f->plan_xs, (size_t)n * gram_row_bytes(f->d, form), s);
+    if (e == cudaSuccess) e = dalloc(&f->plan_ms, (size_t)n, s);
+  }
+  if (e == cudaSuccess && form && f->xform != form) {
+    dfree(f->xb, s);
+    dfree(f->xmeta, s);
+    f->xform = 0;
+    e = dalloc_bytes(&f->xb, (size_t)n * gram_row_bytes(f->d, form), s);
+    if (e == cudaSuccess) e = dalloc(&f->xmeta, (size_t)n, s);
+    if (e == cudaSuccess) {
+      launch_prepare_operands(f->x, n, f->d, form, f->xb, f->xmeta, s);
+      f->xform = form;
+    }
+  }
+  if (e != cudaSuccess) {
+    dfree(f->plan_li, s);
+    dfree(f->plan_ld, s);
+    dfree(f->plan_xs, s);
+    dfree(f->plan_ms, s);
+    f->plan_kp = 0;
+    return map_cuda(e);
+  }
+  f->plan_k = k;
+  f->plan_w = w;
+  f->plan_kp = kp;
+  f->plan_nt = threads;
+  f->plan_form = form;
+  return finish(f, s);
+}
+
+// Enqueues list init, per tree the window launches (plain) or the row gather
+// and the Gram band launch (tensor forms), the re-rank (tensor forms) and
+// the copy of the first k columns; no allocation, no synchronisation.
+static int enqueue_graph(hf_forest* f, int32_t* out_idx, float* out_dist, cudaStream_t s) {
+  const int64_t n = f->n;
+  const int kp = f->plan_kp, k = f->plan_k, form = f->plan_form;
+  launch_list_init(f->plan_li, f->plan_ld, n * kp, s);
+  int rc = HF_OK;
+  for (int t = 0; t < f->T && rc == HF_OK; ++t) {
+    const uint32_t* sig = f->sigma + (size_t)t * n;
+    if (form) {
+      launch_gather_rows(f->xb, f->xmeta, form, n, f->d, sig, f->plan_xs, f->plan_ms, s);
+      rc = launch_gram_window(form, n, f->d, sig, f->plan_w, nullptr, nullptr, kp, f->plan_li, f->plan_ld, f->err,
+                              f->plan_xs, f->plan_ms, s, f->seg, f->seg_off);
+    } else {
+      rc = launch_window_graph(f->x, n, f->d, sig, f->plan_w, kp, f->plan_li, f->plan_ld, s, f->seg, f->seg_off,
+                               f->plan_nt);
+    }
+  }
+  if (rc == HF_OK && form) rc = launch_rerank(f->x, n, f->d, f->sigma, kp, kp, f->plan_li, f->plan_ld, s);
+  if (rc != HF_OK) return rc;
+  if (out_idx &&
+      cudaMemcpy2DAsync(out_idx, (size_t)k * 4, f->plan_li, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return HF_ECUDA;
+  if (out_dist &&
+      cudaMemcpy2DAsync(out_dist, (size_t)k * 4, f->plan_ld, (size_t)kp * 4, (size_t)k * 4, (size_t)n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return HF_ECUDA;
+  return HF_OK;
+}
+
+int hf_knn_graph_enqueue(hf_forest* f, int32_t* out_idx, float* out_dist, void* stream) {
+  if (!f || !out_idx || !out_dist) return HF_EINVAL;
+  if (!f->plan_li) return HF_ESTATE;
+  if (classify(out_idx) != 1 || classify(out_dist) != 1) return HF_EINVAL;
+  return enqueue_graph(f, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+int hf_status(hf_forest* f, void* stream) {
+  if (!f) return HF_EINVAL;
+  return finish(f, static_cast<cudaStream_t>(stream));
+}
+
+int hf_capture_begin(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!s) return HF_EINVAL;  // the legacy default stream cannot be captured
+  return map_cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+}
+
+int hf_capture_end(void* stream, void** exec) {
+  if (!exec) return HF_EINVAL;
+  *exec = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g);
+  if (e != cudaSuccess) return map_cuda(e);
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return map_cuda(e);
+  *exec = x;
+  return HF_OK;
+}
+
+int hf_graph_launch(void* exec, void* stream) {
+  if (!exec) return HF_EINVAL;
+  return map_cuda(cudaGraphLaunch(static_cast<cudaGraphExec_t>(exec), static_cast<cudaStream_t>(stream)));
+}
+
+int hf_graph_destroy(void* exec) {
+  if (!exec) return HF_OK;
+  return map_cuda(cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(exec)));
+}
+
+int hf_exact_knn_rows(hf_forest* f, const int64_t* rows, int32_t nrows, int32_t k, int32_t* out_idx,
+                      float* out_dist, void* stream) {
+  if (!f || !rows || !out_idx || !out_dist || nrows < 1 || k < 1 || k > HF_MAX_K) return HF_EINVAL;
+  for (int32_t j = 0; j < nrows; ++j)
+    if (rows[j] < 0 || rows[j] >= f->n) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  int64_t* rd = nullptr;
+  uint32_t* oi = nullptr;
+  float* od = nullptr;
+  cudaError_t e = dalloc(&rd, (size_t)nrows, s);
+  if (e == cudaSuccess) e = dalloc(&oi, (size_t)nrows * k, s);
+  if (e == cudaSuccess) e = dalloc(&od, (size_t)nrows * k, s);
+  int rc = map_cuda(e);
+  if (rc == HF_OK) rc = map_cuda(cudaMemcpyAsync(rd, rows, (size_t)nrows * 8, cudaMemcpyHostToDevice, s));
+  if (rc == HF_OK) rc = launch_exact_rows(f, rd, nrows, k, oi, od, s);
+  if (rc == HF_OK) rc = map_cuda(cudaMemcpyAsync(out_idx, oi, (size_t)nrows * k * 4, cudaMemcpyDefault, s));
+  if (rc == HF_OK) rc = map_cuda(cudaMemcpyAsync(out_dist, od, (size_t)nrows * k * 4, cudaMemcpyDefault, s));
+  const int rc2 = finish(f, s);
+  dfree(rd, s);
+  dfree(oi, s);
+  dfree(od, s);
+  return rc != HF_OK ? rc : rc2;
+}
+
+int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, int32_t w_max, int32_t forms,
+                int32_t* out_form, int32_t* out_w, int32_t* out_threads, double* out_recall, float* out_ms,
+                void* stream) {
+  if (!f || k < 1 || k > HF_MAX_K || sample < 1 || w_max < 1 || !(target_recall >= 0.0 && target_recall <= 1.0) ||
+      (forms & 7) == 0 || (forms & ~7))
+    return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int ladder_all[] = {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 704, 1024, 1536, 2048};
+  // sample rows spread evenly over the matrix (so over the sets by size)
+  const int m = (int)(sample < f->n ? sample : f->n);
+  std::vector<int64_t> rows(m);
+  for (int j = 0; j < m; ++j) rows[j] = (int64_t)(((__int128)j * f->n) / m);
+  std::vector<int32_t> ex((size_t)m * k);
+  std::vector<float> exd((size_t)m * k);
+  int rc = hf_exact_knn_rows(f, rows.data(), m, k, ex.data(), exd.data(), stream);
+  if (rc != HF_OK) return rc;
+  int64_t* rd = nullptr;
+  uint32_t* got_d = nullptr;
+  cudaError_t e = dalloc(&rd, (size_t)m, s);
+  if (e == cudaSuccess) e = dalloc(&got_d, (size_t)m * k, s);
+  rc = map_cuda(e);
+  if (rc == HF_OK) rc = map_cuda(cudaMemcpyAsync(rd, rows.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+  std::vector<uint32_t> got((size_t)m * k);
+  auto recall_at = [&](int w, double* rec) -> int {
+    int r = hf_graph_plan(f, k, w, 0, stream);
+    if (r == HF_OK) r = enqueue_graph(f, nullptr, nullptr, s);
+    if (r == HF_OK) launch_gather_list_rows(f->plan_li, f->plan_kp, rd, m, k, got_d, s);
+    if (r == HF_OK) r = map_cuda(cudaMemcpyAsync(got.data(), got_d, got.size() * 4, cudaMemcpyDeviceToHost, s));
+    const int r2 = finish(f, s);
+    if (r != HF_OK) return r;
+    if (r2 != HF_OK) return r2;
+    int64_t hit = 0, tot = 0;
+    for (int j = 0; j < m; ++j) {
+      const int32_t* ej = ex.data() + (size_t)j * k;
+      const uint32_t* gj = got.data() + (size_t)j * k;
+      for (int a = 0; a < k; ++a) {
+        if (ej[a] < 0) continue;
+        ++tot;
+        for (int b = 0; b < k; ++b)
+          if (gj[b] == (uint32_t)ej[a]) {
+            ++hit;
+            break;
+          }
+      }
+    }
+    *rec = tot ? (double)hit / (double)tot : 1.0;
+    return HF_OK;
+  };
+  // CUDA-event time of the planned graph (mean of 3 after a warm-up)
+  auto time_plan = [&](float* ms_out) -> int {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int r = enqueue_graph(f, nullptr, nullptr, s);
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3 && r == HF_OK; ++rep) r = enqueue_graph(f, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    const int r2 = finish(f, s);
+    float ms = 0.f;
+    if (r == HF_OK && r2 == HF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) r = HF_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = ms / 3.f;
+    return r != HF_OK ? r : r2;
+  };
+  const int mode0 = f->mode;
+  int best_form = -1, best_w = 0, best_nt = 0;
+  double best_rec = -1.0;
+  float best_ms = 0.f;
+  bool best_hit = false;
+  for (int form = 0; form < 3 && rc == HF_OK; ++form) {
+    if (!(forms & (1 << form))) continue;
+    f->mode = form;
+    std::vector<int> ladder;
+    for (int w : ladder_all)
+      if (w <= w_max && (form == 0 ? w <= HF_PLAIN_MAX_W : gram_supported(f->d, w, form) != 0)) ladder.push_back(w);
+    if (ladder.empty()) continue;
+    // smallest rung reaching the target (recall grows with w)
+    int lo = 0, hi = (int)ladder.size() - 1, pick = hi;
+    double pick_rec = -1.0;
+    while (rc == HF_OK && lo <= hi) {
+      const int mid = (lo + hi) / 2;
+      double rec = 0.0;
+      rc = recall_at(ladder[mid], &rec);
+      if (rc != HF_OK) break;
+      if (rec >= target_recall) {
+        pick = mid;
+        pick_rec = rec;
+        hi = mid - 1;
+      } else {
+        lo = mid + 1;
+      }
+    }
+    if (rc != HF_OK) break;
+    const bool hit = pick_rec >= 0.0;
+    if (!hit) rc = recall_at(ladder[pick], &pick_rec);
+    if (rc != HF_OK) break;
+    // block size (plain form: 256 or 512 threads; the Gram kernel is persistent)
+    const int nts[2] = {256, 512};
+    for (int v = 0; v < (form == 0 ? 2 : 1) && rc == HF_OK; ++v) {
+      const int nt = form == 0 ? nts[v] : 0;
+      if (hf_graph_plan(f, k, ladder[pick], nt, stream) != HF_OK) continue;
+      float ms = 0.f;
+      if (time_plan(&ms) != HF_OK) {
+        cudaGetLastError();  // a block size whose blocks cannot hold 32 positions is skipped
+        continue;
+      }
+      // a form that reaches the target beats one that does not; then time
+      const bool better = best_form < 0 || (hit && !best_hit) ||
+                          (hit == best_hit && (hit ? ms < best_ms : pick_rec > best_rec));
+      if (better) {
+        best_form = form;
+        best_w = ladder[pick];
+        best_nt = nt;
+        best_rec = pick_rec;
+        best_ms = ms;
+        best_hit = hit;
+      }
+    }
+  }
+  if (rc == HF_OK && best_form < 0) rc = HF_ENOTIMPL;
+  if (rc == HF_OK) {
+    f->mode = best_form;
+    rc = hf_graph_plan(f, k, best_w, best_nt, stream);
+  } else {
+    f->mode = mode0;
+  }
+  dfree(rd, s);
+  dfree(got_d, s);
+  if (rc == HF_OK) {
+    if (out_form) *out_form = best_form;
+    if (out_w) *out_w = best_w;
+    if (out_threads) *out_threads = best_nt;
+    if (out_recall) *out_recall = best_rec;
+    if (out_ms) *out_ms = best_ms;
+  }
+  return rc;
 }
 
 int hf_set_sketch(hf_forest* f, const float* R, int32_t bits, void* stream) {
@@ -699,6 +1039,7 @@ int hf_budget_labels(hf_forest* f, const int32_t* knn, int32_t k, const int32_t*
   if (!f || !knn || !t_grid || !w_grid || !out_targets || !out_cell || k < 1 || k > HF_MAX_K || nt < 1 || nw < 1 ||
       nt > 16 || nw > 16 || min_hits < 0 || min_hits > k)
     return HF_EINVAL;
+  if (f->nseg > 1) return HF_ENOTIMPL;
   if (classify(knn) != 1 || classify(out_targets) != 1 || classify(out_cell) != 1) return HF_EINVAL;
   int tmax = 0;
   for (int i = 0; i < nt; ++i) {
@@ -770,6 +1111,7 @@ static int sketch_search(hf_forest* f, const float* q, const uint8_t* qc, int64_
 int hf_search(hf_forest* f, const float* queries, int64_t nq, int32_t k, int32_t w, int32_t* out_idx,
               float* out_dist, void* stream) {
   if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
+  if (f->nseg > 1) return HF_ENOTIMPL;
   if (nq == 0) return HF_OK;
   if (!queries || !out_idx || !out_dist || nq > HF_MAX_N) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -861,6 +1203,7 @@ int hf_debug_order(hf_forest* f, int32_t tree, uint32_t* out_sigma, void* stream
 int hf_debug_locate(hf_forest* f, int32_t tree, const float* queries, int64_t nq, int64_t* out_pos,
                     void* stream) {
   if (!f || tree < 0 || tree >= f->T || nq < 0) return HF_EINVAL;
+  if (f->nseg > 1) return HF_ENOTIMPL;
   if (nq == 0) return HF_OK;
   if (!queries || !out_pos) return HF_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

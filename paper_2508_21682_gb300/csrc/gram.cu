@@ -230,6 +230,8 @@ struct GramArgs {
   const uint32_t* sigma;   // order of this tree: position -> point
   const int32_t* tile_w;   // per-tile window of this tree, or null (uniform w)
   const uint16_t* pw;      // per-point window, or null (uniform w)
+  const uint32_t* segr;    // segmented forest: set of each point, or null
+  const int64_t* segoff;   // segmented forest: first position of each set (+ end)
   int64_t n;
   int nk;                  // K chunks of 128 bytes per row
   int elem_per_chunk;      // 64 (BF16) or 128 (FP8) elements per chunk
@@ -614,6 +616,15 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __gr
           // the row's band: columns [r + W8 - wr, r + W8 + wr] except r + W8
           wlo = r + g.W8 - wr;
           whi = rowok ? r + g.W8 + wr : -1;
+          if (rowok && a.segr) {
+            // segmented forest: only the positions of the row's own set
+            // (column c is position t * GB - W8 + c)
+            const uint32_t sg = __ldg(a.segr + ip);
+            const int64_t cbase = t * GB - g.W8;
+            const int64_t plo = __ldg(a.segoff + sg) - cbase, phi = __ldg(a.segoff + sg + 1) - 1 - cbase;
+            if (plo > wlo) wlo = (int)plo;
+            if (phi < whi) whi = (int)phi;
+          }
           // both halves start from the point's list (fetched while the MMAs
           // run), so both screen against its current last entry; half 0
           // writes the merged list back
@@ -974,7 +985,7 @@ void launch_gather_rows(const void* xq, const float2* meta, int form, int64_t n,
 
 int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w, const int32_t* tile_w,
                        const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err, const void* xs, const float2* ms,
-                       cudaStream_t s) {
+                       cudaStream_t s, const uint32_t* segr, const int64_t* segoff) {
   const bool f8 = form == 2;
   const GramPlan p = gram_plan(d, w, f8, max_smem_optin());
   if (!p.ok) return HF_EINVAL;
@@ -986,6 +997,8 @@ int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w,
   a.sigma = sigma;
   a.tile_w = tile_w;
   a.pw = pw;
+  a.segr = segr;
+  a.segoff = segoff;
   a.n = n;
   a.nk = p.nk;
   a.elem_per_chunk = f8 ? 128 : 64;

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 #include <string>
@@ -52,8 +54,8 @@ struct hf_forest {
   const float* x = nullptr;  // n x d float32, device
   float* x_owned = nullptr;  // device copy when the caller passed host memory
 
-  float* lo = nullptr;        // [d]
-  float* scale = nullptr;     // [d]
+  float* lo = nullptr;        // [nseg][d]
+  float* scale = nullptr;     // [nseg][d]
   uint32_t* planes = nullptr; // [bits][n][W32]; plane 0 = most significant bit
 
   int32_t* pi = nullptr;      // [T][d]
@@ -75,6 +77,14 @@ struct hf_forest {
   float* xm = nullptr;        // master-ordered points (n x d), built on demand
   uint32_t* posm = nullptr;   // inverse of the master order
 
+  // segmented forest: rows seg_off[s] .. seg_off[s+1]-1 are independent set
+  // s (own range, own windows); every order lists set 0's points first, then
+  // set 1's, ... (each set in its own Hilbert order)
+  int nseg = 1;
+  int64_t* seg_off = nullptr;  // [nseg + 1], device
+  uint32_t* seg = nullptr;     // [n] set of each row, device
+  std::vector<int64_t> seg_off_h;
+
   uint64_t* pk = nullptr;     // [TB][K2][n] key words in point order (scratch)
   uint32_t* p0t = nullptr;    // [ceil(n/32)][d] bit-sliced plane 0 (scratch, top-level prefix path)
   int TB = 1;                 // trees keyed and sorted together
@@ -87,6 +97,12 @@ struct hf_forest {
   int sort_batch_max = 0;  // cap on trees per sort batch (0: by memory)
   int mode = 0;
   int tensor_slack = -1;  // extra list slots kept for the re-rank (-1: k)
+  // enqueue-only graph plan (hf_graph_plan / hf_autotune)
+  uint32_t* plan_li = nullptr;
+  float* plan_ld = nullptr;
+  void* plan_xs = nullptr;     // tensor forms: operand rows in tree order
+  float2* plan_ms = nullptr;
+  int plan_k = 0, plan_w = 0, plan_kp = 0, plan_nt = 0, plan_form = 0;
   int sketch_k2 = 60;     // candidates kept by Hamming distance (mode 3)
   int expand_h = 2;       // master-order neighbours per survivor (mode 3 search)
   int timing = 1;
@@ -101,8 +117,13 @@ struct hf_forest {
 void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int bits,
                   int* err, void* scratch, size_t scratch_bytes, cudaStream_t s);
 size_t range_scratch_bytes(int64_t n, int d);
+// segmented matrix (rows off[s] .. off[s+1]-1 form set s): per-set range
+// (lo / scale: nseg x d) and the set of every row
+void launch_seg_range(const float* x, int d, const int64_t* off, int nseg, int bits, float* lo, float* scale, int* err,
+                      cudaStream_t s);
+void launch_seg_of_row(const int64_t* off, int nseg, int64_t n, uint32_t* seg, uint64_t* seg64, cudaStream_t s);
 void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
-                            int bits, uint32_t* planes, int* err, cudaStream_t s);
+                            int bits, uint32_t* planes, int* err, cudaStream_t s, const uint32_t* seg = nullptr);
 void launch_quantize_codes(const float* x, int64_t n, int d, const float* lo, const float* scale,
                            int bits, uint8_t* codes, int* err, cudaStream_t s);
 void launch_planes_to_codes(const uint32_t* planes, int64_t n, int d, int bits, uint8_t* codes,
@@ -124,16 +145,21 @@ void launch_full_keys_codes(const uint8_t* codes, int64_t n, int d, int bits, in
 
 // sort.cu
 int sort_batch(hf_forest* f, int t0, int tb, cudaStream_t s);  // keys of trees t0.. -> sigma, prefix
+// segmented forest: stable partition of every tree's order by the set of its
+// point (seg64: the set of each point as a 64-bit key), after the fix-ups
+int segment_pass(hf_forest* f, const uint64_t* seg64, cudaStream_t s);
 int tie_fixup_big(hf_forest* f, int tree, uint32_t big_runs, cudaStream_t s);
 
 // window.cu
 int window_list_pitch(int k);  // list slots per point kept by the window kernel (>= k)
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
-                        uint32_t* list_idx, float* list_dist, cudaStream_t s);
+                        uint32_t* list_idx, float* list_dist, cudaStream_t s,
+                        const uint32_t* segr = nullptr, const int64_t* segoff = nullptr, int nt = 0);
 void launch_list_init(uint32_t* idx, float* dist, int64_t count, cudaStream_t s);
 // the same over binary sketches (words 32-bit words per point), Hamming distance
 int launch_window_hamming(const uint32_t* sketch, int64_t n, int words, const uint32_t* sigma, int w, int kp,
-                          uint32_t* list_idx, float* list_dist, cudaStream_t s);
+                          uint32_t* list_idx, float* list_dist, cudaStream_t s,
+                          const uint32_t* segr = nullptr, const int64_t* segoff = nullptr);
 
 // gram.cu -- tensor-core window distances. form 1: BF16 operands; form 2:
 // FP8 e4m3 operands with one scale per vector.
@@ -152,7 +178,8 @@ void launch_gather_rows(const void* xq, const float2* meta, int form, int64_t n,
 // then every point uses w
 int launch_gram_window(int form, int64_t n, int d, const uint32_t* sigma, int w, const int32_t* tile_w,
                        const uint16_t* pw, int kp, uint32_t* li, float* ld, int* err, const void* xs, const float2* ms,
-                       cudaStream_t s);
+                       cudaStream_t s,
+                       const uint32_t* segr = nullptr, const int64_t* segoff = nullptr);
 // exact float32 re-rank of the first kc slots of each KP-slot list
 int launch_rerank(const float* x, int64_t n, int d, const uint32_t* order, int kp, int kc, uint32_t* li, float* ld,
                   cudaStream_t s);
@@ -184,6 +211,11 @@ int launch_sketch_search(const hf_forest* f, const float* q, int64_t nq, const i
                          int k, int w, int k2, int h, uint32_t* out_idx, float* out_dist, cudaStream_t s);
 void launch_master_layout(const float* x, int64_t n, int d, const uint32_t* sig0, float* xm, uint32_t* posm,
                           cudaStream_t s);
+// exact k nearest of given rows (device int64) among their own set's points
+int launch_exact_rows(const hf_forest* f, const int64_t* rows, int nrows, int k, uint32_t* out_idx, float* out_dist,
+                      cudaStream_t s);
+void launch_gather_list_rows(const uint32_t* lists, int kp, const int64_t* rows, int nrows, int k, uint32_t* out,
+                             cudaStream_t s);
 
 // host helpers (api.cu)
 void hf_tree_params_host(uint64_t seed, int tree, int d, int32_t* pi, uint8_t* r);

@@ -129,8 +129,9 @@ __device__ __forceinline__ uint64_t transpose8x8(uint64_t x) {
 constexpr int QP_THREADS = 256;
 
 __global__ void __launch_bounds__(QP_THREADS)
-quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, const float* __restrict__ lo,
-                       const float* __restrict__ scale, int bits, int vec4, uint32_t* __restrict__ planes) {
+quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, const float* __restrict__ lo0,
+                       const float* __restrict__ scale0, int bits, int vec4, const uint32_t* __restrict__ seg,
+                       uint32_t* __restrict__ planes) {
   extern __shared__ __align__(16) float qsm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int rowf = 32 * W32;                       // staged floats (>= d)
@@ -143,6 +144,10 @@ quantize_planes_kernel(const float* __restrict__ x, int64_t n, int d, int W32, c
   const int groups = 4 * W32;
   for (int64_t i = warp; i < n; i += nwarps) {
     const float* row = x + (size_t)i * d;
+    // segmented rows take their own set's range
+    const size_t so = seg ? (size_t)__ldg(seg + i) * d : 0;
+    const float* __restrict__ lo = lo0 + so;
+    const float* __restrict__ scale = scale0 + so;
     if (vec4) {
       for (int f = lane; f < (d >> 2); f += 32)
         reinterpret_cast<float4*>(row_s)[f] = __ldg(reinterpret_cast<const float4*>(row) + f);
@@ -216,6 +221,57 @@ __global__ void planes_to_codes_kernel(const uint32_t* __restrict__ planes, int6
   }
 }
 
+// Range of every set of a segmented matrix: block (set, 32-column chunk);
+// lane j of each warp keeps the min / max of column 32 c + j over the warp's
+// rows of the set, then the block's warps are combined. Same lo / scale
+// formula as range_final_kernel.
+__global__ void seg_range_kernel(const float* __restrict__ x, int d, const int64_t* __restrict__ off, int nchunks,
+                                 int bits, float* __restrict__ lo, float* __restrict__ scale, int* __restrict__ err) {
+  __shared__ float smn[8][32], smx[8][32];
+  const int set = blockIdx.x / nchunks, ch = blockIdx.x % nchunks;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = 32 * ch + lane;
+  const int64_t r0 = off[set], r1 = off[set + 1];
+  float mn = INFINITY, mx = -INFINITY;
+  bool bad = false;
+  if (c < d) {
+    for (int64_t r = r0 + warp; r < r1; r += 8) {
+      const float v = __ldg(x + (size_t)r * d + c);
+      bad |= !isfinite(v);
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+    }
+  }
+  if (bad) hf_raise(err, HF_ERRBIT_NONFINITE);
+  smn[warp][lane] = mn;
+  smx[warp][lane] = mx;
+  __syncthreads();
+  if (warp == 0 && c < d) {
+    for (int w = 1; w < 8; ++w) {
+      mn = fminf(mn, smn[w][lane]);
+      mx = fmaxf(mx, smx[w][lane]);
+    }
+    lo[(size_t)set * d + c] = mn;
+    const float width = __fsub_rn(mx, mn);
+    scale[(size_t)set * d + c] = width > 0.0f ? (float)((double)(1u << bits) / (double)width) : 0.0f;
+  }
+}
+
+// Set index of every row of a segmented matrix (binary search of the offsets).
+__global__ void seg_of_row_kernel(const int64_t* __restrict__ off, int nseg, int64_t n, uint32_t* __restrict__ seg,
+                                  uint64_t* __restrict__ seg64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nseg - 1;  // last set whose offset is <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(off + mid) <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    seg[i] = (uint32_t)lo;
+    if (seg64) seg64[i] = (uint64_t)lo;
+  }
+}
+
 int64_t range_threads(int64_t n, int d, int vec) {
   const int64_t groups = d / vec;
   int64_t target = 152 * 2048;
@@ -253,8 +309,20 @@ void launch_range(const float* x, int64_t n, int d, float* lo, float* scale, int
   hf_after_launch("range_final_kernel", s);
 }
 
+void launch_seg_range(const float* x, int d, const int64_t* off, int nseg, int bits, float* lo, float* scale, int* err,
+                      cudaStream_t s) {
+  const int nchunks = (d + 31) / 32;
+  seg_range_kernel<<<(unsigned)(nseg * nchunks), 256, 0, s>>>(x, d, off, nchunks, bits, lo, scale, err);
+  hf_after_launch("seg_range_kernel", s);
+}
+
+void launch_seg_of_row(const int64_t* off, int nseg, int64_t n, uint32_t* seg, uint64_t* seg64, cudaStream_t s) {
+  seg_of_row_kernel<<<hf_blocks(n, 256, 152 * 8), 256, 0, s>>>(off, nseg, n, seg, seg64);
+  hf_after_launch("seg_of_row_kernel", s);
+}
+
 void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, const float* scale,
-                            int bits, uint32_t* planes, int* err, cudaStream_t s) {
+                            int bits, uint32_t* planes, int* err, cudaStream_t s, const uint32_t* seg) {
   (void)err;
   const int W32 = (d + 31) / 32;
   const int vec4 = d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
@@ -262,7 +330,7 @@ void launch_quantize_planes(const float* x, int64_t n, int d, const float* lo, c
   if (smem > 48 * 1024)
     cudaFuncSetAttribute((const void*)quantize_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   quantize_planes_kernel<<<hf_blocks(n * 32, QP_THREADS, 152 * 16), QP_THREADS, smem, s>>>(x, n, d, W32, lo, scale,
-                                                                                          bits, vec4, planes);
+                                                                                          bits, vec4, seg, planes);
   hf_after_launch("quantize_planes_kernel", s);
 }
 

@@ -633,6 +633,108 @@ __global__ void master_layout_kernel(const float* __restrict__ x, int64_t n, int
   }
 }
 
+// Exact k nearest neighbours of given rows among the points of their own set
+// (the whole matrix when unsegmented), the row itself excluded: one warp per
+// row, every point of the set scored 32 at a time with the search's float32
+// exact-difference distance and merged into the warp-held list.
+template <int S>
+__global__ void __launch_bounds__(SWARPS * 32)
+exact_rows_kernel(const float* __restrict__ x, int64_t n, int d, const int64_t* __restrict__ rows, int nrows,
+                  const uint32_t* __restrict__ segr, const int64_t* __restrict__ segoff, int k, int vec4,
+                  uint32_t* __restrict__ out_idx, float* __restrict__ out_dist) {
+  __shared__ uint32_t s_id[SWARPS][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t wi = (int64_t)blockIdx.x * SWARPS + wib;
+  if (wi >= nrows) return;
+  const int64_t r = rows[wi];
+  const float* qv = x + (size_t)r * d;
+  int64_t lo = 0, hi = n;
+  if (segr) {
+    const uint32_t sg = __ldg(segr + r);
+    lo = __ldg(segoff + sg);
+    hi = __ldg(segoff + sg + 1);
+  }
+  WarpList<S> list;
+  list.init();
+  for (int64_t cb = lo; cb < hi; cb += 32) {
+    const int64_t c = cb + lane;
+    uint32_t pid = (c < hi && c != r) ? (uint32_t)c : 0xffffffffu;
+    float dist;
+    if (vec4) {
+      s_id[wib][lane] = pid;
+      __syncwarp();
+      float part[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) part[u] = 0.f;
+      for (int m = 4 * lane; m < d; m += 128) {
+        const float4 qa = __ldg(reinterpret_cast<const float4*>(qv + m));
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += 16) {
+          float4 xb[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const uint32_t p = s_id[wib][u0 + u];
+            const float* row = p != 0xffffffffu ? x + (size_t)p * d : qv;
+            xb[u] = __ldg(reinterpret_cast<const float4*>(row + m));
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            float e = qa.x - xb[u].x;
+            float acc = fmaf(e, e, part[u0 + u]);
+            e = qa.y - xb[u].y;
+            acc = fmaf(e, e, acc);
+            e = qa.z - xb[u].z;
+            acc = fmaf(e, e, acc);
+            e = qa.w - xb[u].w;
+            part[u0 + u] = fmaf(e, e, acc);
+          }
+        }
+      }
+      dist = warp_transpose_sum(part, lane);
+      __syncwarp();
+    } else {
+      dist = 0.f;
+      if (pid != 0xffffffffu) {
+        const float* xv = x + (size_t)pid * d;
+        for (int j = 0; j < d; ++j) {
+          const float e = __ldg(qv + j) - __ldg(xv + j);
+          dist = fmaf(e, e, dist);
+        }
+      }
+    }
+    if (pid == 0xffffffffu) dist = INFINITY;
+    warp_sort(dist, pid, lane);
+    for (int u = 0; u < 32; ++u) {
+      const float cd = __shfl_sync(FULL, dist, u);
+      const uint32_t ci = __shfl_sync(FULL, pid, u);
+      if (ci == 0xffffffffu) break;
+      float kd;
+      uint32_t ki;
+      list.last(k, kd, ki);
+      if (!lessp(cd, ci, kd, ki)) break;
+      list.insert(cd, ci, k, lane);
+    }
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < S; ++s2) {
+    const int e = 32 * s2 + lane;
+    if (e < k) {
+      out_idx[(size_t)wi * k + e] = list.iv[s2];
+      out_dist[(size_t)wi * k + e] = list.dv[s2];
+    }
+  }
+}
+
+// out[j][c] = lists[rows[j]][c] for c < k (lists have kp slots per row).
+__global__ void gather_list_rows_kernel(const uint32_t* __restrict__ lists, int kp, const int64_t* __restrict__ rows,
+                                        int nrows, int k, uint32_t* __restrict__ out) {
+  const int64_t total = (int64_t)nrows * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / k;
+    out[e] = lists[(size_t)rows[j] * kp + (e - j * k)];
+  }
+}
+
 template <int S2, int S>
 int launch_ss(const SketchSearchArgs& a, cudaStream_t s) {
   sketch_search_kernel<S2, S><<<hf_blocks(a.nq, SWARPS), SWARPS * 32, 0, s>>>(a);
@@ -651,6 +753,28 @@ int launch_ss_k2(const SketchSearchArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+int launch_exact_rows(const hf_forest* f, const int64_t* rows, int nrows, int k, uint32_t* out_idx, float* out_dist,
+                      cudaStream_t s) {
+  if (k < 1 || k > 64 || nrows < 1) return HF_EINVAL;
+  const int vec4 = f->d % 4 == 0 && (reinterpret_cast<uintptr_t>(f->x) & 15) == 0;
+  const uint32_t* segr = f->nseg > 1 ? f->seg : nullptr;
+  const int64_t* segoff = f->nseg > 1 ? f->seg_off : nullptr;
+  if (k <= 32)
+    exact_rows_kernel<1><<<hf_blocks(nrows, SWARPS), SWARPS * 32, 0, s>>>(f->x, f->n, f->d, rows, nrows, segr, segoff,
+                                                                          k, vec4, out_idx, out_dist);
+  else
+    exact_rows_kernel<2><<<hf_blocks(nrows, SWARPS), SWARPS * 32, 0, s>>>(f->x, f->n, f->d, rows, nrows, segr, segoff,
+                                                                          k, vec4, out_idx, out_dist);
+  hf_after_launch("exact_rows_kernel", s);
+  return HF_OK;
+}
+
+void launch_gather_list_rows(const uint32_t* lists, int kp, const int64_t* rows, int nrows, int k, uint32_t* out,
+                             cudaStream_t s) {
+  gather_list_rows_kernel<<<hf_blocks((int64_t)nrows * k, 256, 152 * 4), 256, 0, s>>>(lists, kp, rows, nrows, k, out);
+  hf_after_launch("gather_list_rows_kernel", s);
+}
 
 void launch_master_layout(const float* x, int64_t n, int d, const uint32_t* sig0, float* xm, uint32_t* posm,
                           cudaStream_t s) {
@@ -750,6 +874,7 @@ extern "C" int hf_search_static(hf_forest* f, const float* queries, int64_t nq, 
                                 int32_t* out_idx, float* out_dist, void* stream) {
   if (!f || nq < 0 || k < 1 || k > HF_MAX_K || w < 1) return HF_EINVAL;
   if (f->mode == 3) return HF_ENOTIMPL;  // the sketch form needs per-call scratch
+  if (f->nseg > 1) return HF_ENOTIMPL;   // segmented orders carry no search prefixes
   if (nq == 0) return HF_OK;
   if (!queries || !out_idx || !out_dist) return HF_EINVAL;
   if ((uint64_t)nq * (uint64_t)f->d > (uint64_t)HF_STATIC_QUERY_BYTES) return HF_EINVAL;

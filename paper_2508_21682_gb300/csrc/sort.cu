@@ -680,6 +680,53 @@ int sort_batch(hf_forest* f, int t0, int tb, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
 }
 
+// Segmented forest: one more stable LSD pass per tree, keyed by the set of
+// each point (the most significant digit of the order), gathered through the
+// current order. Equal sets keep their relative order, so every set's points
+// stay in their own Hilbert order and set s occupies positions off[s] ..
+// off[s+1]-1. Up to 256 sets (one 8-bit digit).
+int segment_pass(hf_forest* f, const uint64_t* seg64, cudaStream_t s) {
+  const int64_t n = f->n;
+  const int nseg = f->nseg;
+  if (nseg < 2 || nseg > 256) return HF_EINVAL;
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  std::vector<uint32_t> goff(256, (uint32_t)n);
+  for (int g = 0; g < nseg; ++g) goff[g] = (uint32_t)f->seg_off_h[g];
+  if (cudaMemcpyAsync(f->sort.hist, goff.data(), 256 * sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return HF_ECUDA;
+  const size_t psm = sizeof(PassSmem);
+  set_attr((const void*)onesweep_kernel<true>, psm);
+  for (int t0 = 0; t0 < f->T; t0 += f->TB) {
+    const int tb = f->T - t0 < f->TB ? f->T - t0 : f->TB;
+    const size_t words = (size_t)tb * (ntiles + 1) * 256 + 1;
+    cudaMemsetAsync(f->sort.status, 0, words * sizeof(uint32_t), s);
+    PassArgs a{};
+    a.err = f->err;
+    a.n = n;
+    a.ntiles = ntiles;
+    a.spin_ns = (uint64_t)f->spin_limit_us * 1000ull;
+    a.TB = tb;
+    a.vals_in = f->sigma + (size_t)t0 * n;
+    a.vals_in_ts = n;
+    a.gather_src = seg64;
+    a.gather_src_ts = 0;
+    a.keys_out = f->sort.keys_a;
+    a.keys_out_ts = n;
+    a.vals_out = f->sort.vals_a;
+    a.vals_out_ts = n;
+    a.goff = f->sort.hist;
+    a.goff_ts = 0;
+    a.status = f->sort.status;
+    a.ticket = f->sort.status + (size_t)tb * (ntiles + 1) * 256;
+    a.shift = 0;
+    onesweep_kernel<true><<<(unsigned)(ntiles * tb), NT, psm, s>>>(a);
+    hf_after_launch("onesweep_kernel<segment>", s);
+    cudaMemcpyAsync(f->sigma + (size_t)t0 * n, f->sort.vals_a, (size_t)tb * n * sizeof(uint32_t),
+                    cudaMemcpyDeviceToDevice, s);
+  }
+  return cudaGetLastError() == cudaSuccess ? HF_OK : HF_ECUDA;
+}
+
 // Host side of the big-run path; called after the build's sync, when the
 // host knows how many big runs tree t has.
 int tie_fixup_big(hf_forest* f, int t, uint32_t nbig, cudaStream_t s) {

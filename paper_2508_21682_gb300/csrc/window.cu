@@ -92,7 +92,8 @@ __device__ __forceinline__ void stage_chunk(float* buf, int NRP, int NR, const u
 template <int KP, int NT, bool HAM>
 __global__ void __launch_bounds__(NT, 512 / NT)
 window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __restrict__ sigma, int w,
-              int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist) {
+              int B, int dlo, uint32_t* __restrict__ lidx, float* __restrict__ ldist,
+              const uint32_t* __restrict__ segr, const int64_t* __restrict__ segoff) {
   constexpr int ROWS = rows_of(NT);
   extern __shared__ __align__(16) float smem[];
   const int dhi = dlo + WB - 1;
@@ -178,9 +179,16 @@ window_kernel(const float* __restrict__ x, int64_t n, int d, const uint32_t* __r
     const uint32_t ip = srow[rowp];
     ListK<KP> L;
     L.load(ldist + (size_t)ip * KP, lidx + (size_t)ip * KP);
-    const int rmax = (int)(n - 1 - p < wtop ? n - 1 - p : wtop);  // right: (p, p + delta)
+    // positions of p's set (segmented forest: the set's block of the order)
+    int64_t plo = 0, phi = n;
+    if (segr) {
+      const uint32_t sg = __ldg(segr + ip);
+      plo = __ldg(segoff + sg);
+      phi = __ldg(segoff + sg + 1);
+    }
+    const int rmax = (int)(phi - 1 - p < wtop ? phi - 1 - p : wtop);  // right: (p, p + delta)
     for (int delta = dlo; delta <= rmax; ++delta) L.offer(band[rowp * WB + delta - dlo], srow[rowp + delta]);
-    const int lmax = (int)(p < wtop ? p : wtop);  // left: (p - delta, p)
+    const int lmax = (int)(p - plo < wtop ? p - plo : wtop);  // left: (p - delta, p)
     for (int delta = dlo; delta <= lmax; ++delta)
       L.offer(band[(rowp - delta) * WB + delta - dlo], srow[rowp - delta]);
     L.store(ldist + (size_t)ip * KP, lidx + (size_t)ip * KP);
@@ -204,7 +212,7 @@ size_t window_smem(int B, int dhi, int rows) {
 
 template <int KP, int NT, bool HAM>
 int launch_band(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int dlo, uint32_t* li, float* ldd,
-                cudaStream_t s) {
+                cudaStream_t s, const uint32_t* segr, const int64_t* segoff) {
   const int dhi = dlo + WB - 1;
   const int B = rows_of(NT) - dhi;
   const size_t smem = window_smem(B, dhi, rows_of(NT));
@@ -212,18 +220,21 @@ int launch_band(const float* x, int64_t n, int d, const uint32_t* sigma, int w, 
   if (cudaFuncSetAttribute((const void*)window_kernel<KP, NT, HAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return HF_ECUDA;
-  window_kernel<KP, NT, HAM><<<hf_blocks(n, B), NT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd);
+  window_kernel<KP, NT, HAM><<<hf_blocks(n, B), NT, smem, s>>>(x, n, d, sigma, w, B, dlo, li, ldd, segr, segoff);
   hf_after_launch(HAM ? "window_kernel<hamming>" : "window_kernel", s);
   return HF_OK;
 }
 
+// nt: block threads (256 or 512; 0 picks 256 while its blocks keep 32
+// positions, else 512)
 template <int KP, bool HAM>
 int launch_kp(const float* x, int64_t n, int d, const uint32_t* sigma, int w, uint32_t* li, float* ldd,
-              cudaStream_t s) {
+              cudaStream_t s, const uint32_t* segr, const int64_t* segoff, int nt) {
   for (int dlo = 1; dlo <= w; dlo += WB) {
     const int dhi = dlo + WB - 1;
-    const int rc = rows_of(256) - dhi >= 32 ? launch_band<KP, 256, HAM>(x, n, d, sigma, w, dlo, li, ldd, s)
-                                            : launch_band<KP, 512, HAM>(x, n, d, sigma, w, dlo, li, ldd, s);
+    const bool small = nt == 256 || (nt == 0 && rows_of(256) - dhi >= 32);
+    const int rc = small ? launch_band<KP, 256, HAM>(x, n, d, sigma, w, dlo, li, ldd, s, segr, segoff)
+                         : launch_band<KP, 512, HAM>(x, n, d, sigma, w, dlo, li, ldd, s, segr, segoff);
     if (rc != HF_OK) return rc;
   }
   return HF_OK;
@@ -242,22 +253,25 @@ int window_list_pitch(int k) { return k <= 16 ? 16 : (k <= 32 ? 32 : 64); }
 // the staging within shared memory). Lists have window_list_pitch(k) slots
 // per point.
 int launch_window_graph(const float* x, int64_t n, int d, const uint32_t* sigma, int w, int kp,
-                        uint32_t* list_idx, float* list_dist, cudaStream_t s) {
+                        uint32_t* list_idx, float* list_dist, cudaStream_t s, const uint32_t* segr,
+                        const int64_t* segoff, int nt) {
+  if (nt != 0 && nt != 256 && nt != 512) return HF_EINVAL;
   switch (kp) {
-    case 16: return launch_kp<16, false>(x, n, d, sigma, w, list_idx, list_dist, s);
-    case 32: return launch_kp<32, false>(x, n, d, sigma, w, list_idx, list_dist, s);
-    case 64: return launch_kp<64, false>(x, n, d, sigma, w, list_idx, list_dist, s);
+    case 16: return launch_kp<16, false>(x, n, d, sigma, w, list_idx, list_dist, s, segr, segoff, nt);
+    case 32: return launch_kp<32, false>(x, n, d, sigma, w, list_idx, list_dist, s, segr, segoff, nt);
+    case 64: return launch_kp<64, false>(x, n, d, sigma, w, list_idx, list_dist, s, segr, segoff, nt);
     default: return HF_EINVAL;
   }
 }
 
 int launch_window_hamming(const uint32_t* sketch, int64_t n, int words, const uint32_t* sigma, int w, int kp,
-                          uint32_t* list_idx, float* list_dist, cudaStream_t s) {
+                          uint32_t* list_idx, float* list_dist, cudaStream_t s, const uint32_t* segr,
+                          const int64_t* segoff) {
   const float* x = reinterpret_cast<const float*>(sketch);  // staged as raw 32-bit words
   switch (kp) {
-    case 16: return launch_kp<16, true>(x, n, words, sigma, w, list_idx, list_dist, s);
-    case 32: return launch_kp<32, true>(x, n, words, sigma, w, list_idx, list_dist, s);
-    case 64: return launch_kp<64, true>(x, n, words, sigma, w, list_idx, list_dist, s);
+    case 16: return launch_kp<16, true>(x, n, words, sigma, w, list_idx, list_dist, s, segr, segoff, 0);
+    case 32: return launch_kp<32, true>(x, n, words, sigma, w, list_idx, list_dist, s, segr, segoff, 0);
+    case 64: return launch_kp<64, true>(x, n, words, sigma, w, list_idx, list_dist, s, segr, segoff, 0);
     default: return HF_EINVAL;
   }
 }

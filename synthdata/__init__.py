@@ -16,6 +16,9 @@ The generators below stand in for them with the same shapes:
 * ``sketch_projection`` -- the projection matrix of the sign sketches: i.i.d.
   N(0, 1) entries, one row per sketch bit (the random numbers the sketch
   stage draws, passed to both sides as an input).
+* ``batched_sets`` -- many independent point sets: sizes log-uniform in
+  [lo, hi], dimensions drawn from a list, each set a 100-component mixture of
+  its own (the batched workload).
 * ``small_integer_points`` / ``small_integer_projection`` -- integer-valued
   rows (|v| <= 8) and projections (|v| <= 2): every inner product, squared
   distance and BF16 rounding of them is exact in float32, so float decisions
@@ -39,6 +42,7 @@ __all__ = [
     "mixture_params",
     "mixture_queries",
     "sketch_projection",
+    "batched_sets",
     "small_integer_points",
     "small_integer_projection",
     "SEED_DATA",
@@ -64,6 +68,7 @@ _S_ASSIGN = 3
 _S_NOISE = 4
 _S_PROJ = 5
 _S_INT = 6
+_S_SETS = 7
 
 
 def _gen(seed: int, stream: int, block: int) -> np.random.Generator:
@@ -171,3 +176,15 @@ def small_integer_points(n: int, d: int, seed: int = SEED_DATA) -> np.ndarray:
 def small_integer_projection(bits: int, d: int, seed: int = SEED_SKETCH) -> np.ndarray:
     """float32 [bits][d] with integer values in [-2, 2]."""
     return _gen(seed, _S_INT, 1).integers(-2, 3, size=(bits, d)).astype(np.float32)
+
+
+def batched_sets(nsets: int = 64, lo: int = 1000, hi: int = 200_000, dims=(64, 128, 384, 768),
+                 n_components: int = 100, seed: int = SEED_DATA):
+    """[(points float32 [n_s][d_s])] for nsets independent sets: n_s =
+    round(exp(U(ln lo, ln hi))), d_s uniform over dims, each set drawn from a
+    gaussian_mixture of its own (seed derived from the set index)."""
+    g = _gen(seed, _S_SETS, 0)
+    sizes = np.rint(np.exp(g.uniform(np.log(lo), np.log(hi), size=nsets))).astype(np.int64)
+    ds = g.choice(np.asarray(dims, dtype=np.int64), size=nsets)
+    return [gaussian_mixture(int(sizes[i]), int(ds[i]), n_components=n_components, seed=seed * 1000 + 17 + i)
+            for i in range(nsets)]
