@@ -95,6 +95,13 @@ def args():
                    help="T,w,k2 of the sketch-form graph (the paper's first Table 2 row: 80 sorts, k1 = 96, k2 = 60)")
     p.add_argument("--sketch-search", default="128,300,2",
                    help="w,k2,h of the sketch-form search over the main forest")
+    p.add_argument("--workload", default="graph", choices=["graph", "c3"],
+                   help="graph: the kNN-graph step (default); c3: the large search workload (23M x 384, T = 160, "
+                        "w = 50, k = 30, 10k queries), one JSON line of its own")
+    p.add_argument("--c3-n", type=int, default=23_000_000)
+    p.add_argument("--c3-w", default="50,200,710",
+                   help="query windows of the c3 workload (the first is the configured one; the others trace "
+                        "recall against time, 710 being Table 1's k1 = 1420 around each position)")
     p.add_argument("--recall-sweep", default="",
                    help="comma-separated T list x w list, e.g. '8,16,32,64,128,256:16,32,64,128,256': "
                         "print the plain method's recall@k over that (T, w) grid and exit")
@@ -189,7 +196,7 @@ def make_inputs(a, rank):
     return x, q
 
 
-def exact_knn_gpu(xd, rows_d, k, exclude=None, chunk=512):
+def exact_knn_gpu(xd, rows_d, k, exclude=None, chunk=None):
     """Ground truth for the recall figure: float32 inner-product screen on the
     GPU (torch matmul, TF32 off), keep k + 16, re-score in float64 on the host
     with exact coordinate differences, order by (distance, index)."""
@@ -198,6 +205,8 @@ def exact_knn_gpu(xd, rows_d, k, exclude=None, chunk=512):
     nrm = (xd * xd).sum(1)
     out = []
     keep = k + 16
+    if chunk is None:  # the distance block stays near 1 GB
+        chunk = max(1, min(512, (1 << 28) // xd.shape[0]))
     for s in range(0, rows_d.shape[0], chunk):
         q = rows_d[s:s + chunk]
         g = nrm[None, :] + (q * q).sum(1)[:, None] - 2.0 * (q @ xd.T)
@@ -815,6 +824,8 @@ def batched_form(a, hf, dev):
             forests = [hf.build_segmented(g["X"], g["off"], T=T, bits=a.bits, seed=3) for g in groups]
             for G, g in zip(forests, groups):
                 G.set_option("mode", g["tune"]["form"])
+                if g["tune"]["form"]:
+                    G.set_option("tensor_slack", g["tune"]["list_slots"] - k)
                 G.graph_plan(k, g["tune"]["w"], g["tune"]["threads"], side.cuda_stream)
             graph = None
             if capture_graph:
@@ -866,6 +877,7 @@ def batched_form(a, hf, dev):
     # the same sets one at a time
     wmap = {g["d"]: g["tune"]["w"] for g in groups}
     fmap = {g["d"]: g["tune"]["form"] for g in groups}
+    smap = {g["d"]: g["tune"]["list_slots"] for g in groups}
     xs = [torch.from_numpy(x).to(dev) for x in sets]
     one_ms = []
     l0 = hf.launch_count()
@@ -874,6 +886,8 @@ def batched_form(a, hf, dev):
         e0 = ev(torch.cuda.current_stream(dev))
         G = hf.build(x, T=T, bits=a.bits, seed=3)
         G.set_option("mode", fmap[x.shape[1]])
+        if fmap[x.shape[1]]:
+            G.set_option("tensor_slack", smap[x.shape[1]] - k)
         G.knn_graph(k, wmap[x.shape[1]])
         e1 = ev(torch.cuda.current_stream(dev))
         torch.cuda.synchronize(dev)
@@ -975,10 +989,84 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_c3(a):
+    """The large search workload: n points (23M by default) x 384 from the
+    mixture, T = 160 trees, b = 8, query window w = 50 on each side (about 100
+    candidates per tree), k = 30, 10,000 mixture queries. One JSON line:
+    queries/s of hf_search (CUDA events, inputs resident), the build's time,
+    recall@30 on 500 queries, and the largest relative error of the returned
+    float32 distances against float64 on 200 queries."""
+    import torch
+    import synthdata as S
+    import __graft_entry__ as g
+    g.build()
+    import paper_2508_21682_gb300 as hf
+
+    n, d, T, k, nq = a.c3_n, 384, 160, 30, 10_000
+    windows = [int(v) for v in a.c3_w.split(",")]
+    w = windows[0]
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    xd = torch.from_numpy(S.gaussian_mixture(n, d, n_components=1000, seed=S.SEED_DATA)).to(dev)
+    qd = torch.from_numpy(S.mixture_queries(nq, d, n_components=1000, data_seed=S.SEED_DATA)).to(dev)
+    gen_s = time.perf_counter() - t0
+    st = torch.cuda.current_stream(dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        return e
+
+    torch.cuda.synchronize()
+    e0 = ev()
+    G = hf.build(xd, T=T, bits=a.bits, seed=3)
+    e1 = ev()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    ph = G.timings()
+    ex = exact_knn_gpu(xd, qd[:500], k)
+    sweep = []
+    for wv in windows:
+        si, sd = G.search(qd, k, wv)  # warm-up
+        torch.cuda.synchronize()
+        reps = max(3, a.steps)
+        e0 = ev()
+        for _ in range(reps):
+            G.search(qd, k, wv, si, sd)
+        e1 = ev()
+        torch.cuda.synchronize()
+        sweep.append({"w": wv, "ms_per_batch": e0.elapsed_time(e1) / reps,
+                      "queries_per_s": nq / (e0.elapsed_time(e1) / reps * 1e-3),
+                      "recall_at_k": recall(si[:500].cpu().numpy(), ex)})
+        if wv == w:
+            first = (si.clone(), sd.clone())
+    si, sd = first
+    ms, rec = sweep[0]["ms_per_batch"], sweep[0]["recall_at_k"]
+    gi = si[:200].long()
+    diff = xd[gi.clamp(min=0)].double() - qd[:200].double()[:, None, :]
+    true = (diff * diff).sum(-1)
+    ok = gi >= 0
+    err = ((sd[:200].double() - true).abs() / true.clamp(min=1e-30))[ok].max().item()
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    G.close()
+    print(json.dumps({
+        "workload": f"search: n={n}, d={d} float32 mixture (1000 components), T={T}, b={a.bits}, "
+                    f"w={w} on each side, k={k}, {nq} mixture queries",
+        "metric": "queries/s", "value": nq / (ms * 1e-3), "unit": "queries/s", "ms_per_batch": ms,
+        "recall_at_k": rec, "recall_sample": 500, "windows": sweep, "build_ms": build_ms,
+        "build_phase_ms": {kk: ph[kk] for kk in ("quantize", "keys", "sort", "tie_fixup")},
+        "hilbert_sort_mkeys_s": n * T / ((ph["keys"] + ph["sort"] + ph["tie_fixup"]) * 1e-3) / 1e6,
+        "max_rel_dist_err_vs_f64": err, "generation_s": gen_s, "device_bytes_in_use": int(total_b - free_b),
+        "storage": "float32 rows (the library reads float32; 35 GB at 23M x 384)",
+    }), flush=True)
+
+
 if __name__ == "__main__":
     A = args()
     if A.impl == "reference":
         run_reference(A)
+    elif A.workload == "c3":
+        run_c3(A)
     elif A.recall_sweep:
         recall_sweep(A)
     else:

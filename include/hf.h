@@ -239,10 +239,13 @@ int hf_exact_knn_rows(hf_forest* f, const int64_t* rows, int32_t nrows, int32_t 
  * (recall against hf_exact_knn_rows; it grows with w because the candidate
  * sets grow), found by bisection, and at that w the faster block size of
  * the plain window kernel (256 or 512 threads; the Gram kernel is
- * persistent); then the fastest form that reaches the target (CUDA-event
- * time of the whole graph), else the one with the highest recall. Leaves
- * that form (hf_set_option mode) and plan (hf_graph_plan) in the forest and
- * reports them with the sample recall and the graph's time.
+ * persistent; the Gram forms are tried with 16 and with 32 list slots per
+ * point, i.e. tensor_slack 16 - k and 32 - k, where they hold k + 1); then
+ * the fastest variant that reaches the target (CUDA-event time of the whole
+ * graph), else the one with the highest recall. Leaves that form
+ * (hf_set_option mode, tensor_slack) and plan (hf_graph_plan) in the forest
+ * and reports them with the sample recall and the graph's time; *out_form
+ * is the mode plus 256 x the list slots for a Gram form.
  */
 int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, int32_t w_max, int32_t forms,
                 int32_t* out_form, int32_t* out_w, int32_t* out_threads, double* out_recall, float* out_ms,

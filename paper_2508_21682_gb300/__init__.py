@@ -330,7 +330,8 @@ class Forest:
                                  ctypes.byref(nt), ctypes.byref(rec), ctypes.byref(ms), _stream(self._points)),
                "hf_autotune")
         self.plan_k = int(k)
-        return {"form": fm.value, "w": w.value, "threads": nt.value, "recall": rec.value, "ms": ms.value}
+        return {"form": fm.value & 255, "list_slots": fm.value >> 8, "w": w.value, "threads": nt.value,
+                "recall": rec.value, "ms": ms.value}
 
     def set_sketch(self, R):
         """hf_set_sketch: sketches of all points from the projection R

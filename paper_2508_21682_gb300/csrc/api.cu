@@ -909,14 +909,28 @@ int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, i
     *ms_out = ms / 3.f;
     return r != HF_OK ? r : r2;
   };
-  const int mode0 = f->mode;
-  int best_form = -1, best_w = 0, best_nt = 0;
+  const int mode0 = f->mode, slack0 = f->tensor_slack;
+  int best_form = -1, best_w = 0, best_nt = 0, best_slack = -1;
   double best_rec = -1.0;
   float best_ms = 0.f;
   bool best_hit = false;
-  for (int form = 0; form < 3 && rc == HF_OK; ++form) {
+  // variants: the plain form; each Gram form with the shortest list that
+  // holds k + 1 candidates and with 32 slots (more candidates for the re-rank)
+  struct Variant {
+    int form, slack;
+  };
+  std::vector<Variant> variants;
+  if (forms & 1) variants.push_back({0, -1});
+  for (int form = 1; form <= 2; ++form) {
     if (!(forms & (1 << form))) continue;
+    if (k + 1 <= 16) variants.push_back({form, 16 - k});
+    if (k + 1 <= 32) variants.push_back({form, 32 - k});
+  }
+  for (const Variant& var : variants) {
+    if (rc != HF_OK) break;
+    const int form = var.form;
     f->mode = form;
+    f->tensor_slack = var.slack;
     std::vector<int> ladder;
     for (int w : ladder_all)
       if (w <= w_max && (form == 0 ? w <= HF_PLAIN_MAX_W : gram_supported(f->d, w, form) != 0)) ladder.push_back(w);
@@ -956,6 +970,7 @@ int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, i
                           (hit == best_hit && (hit ? ms < best_ms : pick_rec > best_rec));
       if (better) {
         best_form = form;
+        best_slack = var.slack;
         best_w = ladder[pick];
         best_nt = nt;
         best_rec = pick_rec;
@@ -967,14 +982,16 @@ int hf_autotune(hf_forest* f, int32_t k, double target_recall, int32_t sample, i
   if (rc == HF_OK && best_form < 0) rc = HF_ENOTIMPL;
   if (rc == HF_OK) {
     f->mode = best_form;
+    f->tensor_slack = best_slack;
     rc = hf_graph_plan(f, k, best_w, best_nt, stream);
   } else {
     f->mode = mode0;
+    f->tensor_slack = slack0;
   }
   dfree(rd, s);
   dfree(got_d, s);
   if (rc == HF_OK) {
-    if (out_form) *out_form = best_form;
+    if (out_form) *out_form = best_form | (best_form ? (f->plan_kp << 8) : 0);
     if (out_w) *out_w = best_w;
     if (out_threads) *out_threads = best_nt;
     if (out_recall) *out_recall = best_rec;
