@@ -48,8 +48,8 @@ MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 # DRAM traffic of the dominant kernels from one ncu capture of a 1M-point
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
-WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "17ad84a8c61fc969", "file": "window.cu"}   # w = 32
-GRAM_TRAFFIC = {"bytes_per_point": 1131, "source_sha": "eb33dfa67f0cefa9", "file": "gram.cu"}     # w = 512
+WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "cd0725673dcf443f", "file": "window.cu"}   # w = 32
+GRAM_TRAFFIC = {"bytes_per_point": 1131, "source_sha": "8c23e4b9990306d4", "file": "gram.cu"}     # w = 512
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
