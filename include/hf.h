@@ -81,9 +81,9 @@ enum {
 
 /*
  * hf_build -- preprocessing and the per-tree orders.
- * Paper: Algorithm 2, "randomly permute coordinate axes" and "compute Hilbert
- * order of all points" for each sort; Algorithm 1, "Build n Hilbert trees with
- * randomized axis orders"; Section 2 (Hilbert sort, Hilbert tree as the
+ * Paper: Algorithm 2 (every sort shuffles the coordinate axes, then orders
+ * all points along the curve); Algorithm 1 (the search's trees are built on
+ * shuffled axis orders); Section 2 (Hilbert sort, and the Hilbert tree as the
  * sorted sequence that binary search runs on).
  *
  * points : n x d float32, row-major (point i at points + i*d). Borrowed when

@@ -16,10 +16,10 @@ Paper passages used
 * Section 2: Hilbert sort orders points along a Hilbert curve; the order is a
   total order, so binary search locates an arbitrary point in it; a Hilbert
   forest is several such orders.
-* Algorithm 2 (Section 4, kNN graph): per sort t, randomly permute the axes,
-  compute the Hilbert order, and for the i-th point of the order add the
-  k1 neighbours around position i to its candidate set C1; finally select the
-  top k by vector distance.
+* Algorithm 2 (Section 4, kNN graph): every sort first shuffles the
+  coordinate axes and orders all points along the curve; each point gains as
+  candidates the points that sit within a window around it in that order; the
+  result keeps, per point, the k candidates nearest by vector distance.
 * Algorithm 1 (Section 3, search): per tree, locate each query in the Hilbert
   order and add the candidates near its position; select the top k by vector
   distance.
@@ -85,8 +85,8 @@ def quantize(x: np.ndarray, lo: np.ndarray, scale: np.ndarray, bits: int) -> np.
 
 
 # --------------------------------------------------------------------------
-# Per-tree random axis order (Algorithm 2 "randomly permute coordinate axes";
-# Algorithm 1 "n Hilbert trees with randomized axis orders")
+# Per-tree random axis order (Algorithm 2 shuffles the axes before every sort;
+# Algorithm 1 builds its trees on shuffled axis orders)
 # --------------------------------------------------------------------------
 class SplitMix64:
     """splitmix64: state advances by the golden-ratio constant; the output is
