@@ -614,11 +614,12 @@ def learned_form(a, hf, xd, qd, rows, ex, si, sd, stream, dev):
     ei, _ = E.knn_graph(k, ns)
     E.close()
     tg, wg = [4, 8, 16, 32, 64], [8, 16, 32, 64, 128]
-    ys = []
+    ys, last = [], []
     for r in range(a.label_forests):
         Gs = hf.build(xs, T=tg[-1], bits=a.bits, seed=100 + r)
-        tgt, _ = Gs.budget_labels(ei, tg, wg, 12)
+        tgt, cells = Gs.budget_labels(ei, tg, wg, 12)
         ys.append(tgt)
+        last.append(float((cells == len(tg) * len(wg) - 1).float().mean().item()))
         Gs.close()
     gen = torch.Generator(device="cpu").manual_seed(5)
     perm = torch.randperm(ns * len(ys), generator=gen).to(dev)
@@ -714,7 +715,8 @@ def learned_form(a, hf, xd, qd, rows, ex, si, sd, stream, dev):
             "mean_w": float(w_pt.double().mean()),
             "mean_T": float(t_pt.double().mean()), "band_cost_vs_fixed": cost / ucost,
             "train": {"labels": ns * len(ys), "label_sample": ns, "forests": len(ys), "steps": a.train_steps,
-                      "batch": 1024, "final_loss": loss, "labels_s": labels_s, "train_s": train_s},
+                      "batch": 1024, "final_loss": loss, "labels_s": labels_s, "train_s": train_s,
+                      "labels_at_largest_cell": float(np.mean(last))},
             "model": "MLP d-256-256-2, GELU, BF16 weights/activations, FP32 accumulation (tcgen05), Adam"}
 
 

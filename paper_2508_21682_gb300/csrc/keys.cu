@@ -68,32 +68,56 @@ __global__ void plane0_slice_kernel(const uint32_t* __restrict__ plane0, int64_t
 // plus the running carry of the earlier halves gives key bit i for all 32
 // points, and the transpose (bit-reversed: the key is packed most significant
 // bit first) gives point j its 32 bits 32h .. 32h+31.
+template <int H>
 __global__ void prefix_sliced_kernel(const uint32_t* __restrict__ p0t, int64_t n, int d, int K,
                                      const int32_t* __restrict__ pi, const uint32_t* __restrict__ rbits,
                                      uint64_t* __restrict__ pk) {
+  constexpr int GW = 2;  // point groups per warp and round: their loads are in flight together
   const int lane = threadIdx.x & 31;
   const int64_t G = (n + 31) / 32;
-  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G;
-       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const uint32_t* row = p0t + (size_t)g * d;
-    const int64_t p = g * 32 + lane;
-    uint32_t carry = 0, hi = 0;
-    for (int h = 0; h < 2 * K; ++h) {
-      const int i = 32 * h + lane;
-      uint32_t v = __ldg(row + __ldg(pi + i));
-      if ((__ldg(rbits + h) >> lane) & 1u) v = ~v;
+  const int nh = 2 * K;  // 32-bit halves of the prefix (nh <= H)
+  // the tree's permuted axes and reflection bits of this lane, once per warp
+  int ax[H];
+  uint32_t flip[H];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v ^= t;
-      }
-      v ^= carry;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-      const uint32_t half = __brev(warp_transpose32(v, lane));
-      if (h & 1) {
-        if (p < n) pk[(size_t)(h >> 1) * n + p] = ((uint64_t)hi << 32) | half;
-      } else {
-        hi = half;
+  for (int h = 0; h < H; ++h) {
+    ax[h] = h < nh ? __ldg(pi + 32 * h + lane) : 0;
+    flip[h] = h < nh ? 0u - ((__ldg(rbits + h) >> lane) & 1u) : 0u;
+  }
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g0 < G; g0 += GW * nw) {
+    // every word of both groups is loaded before any is used
+    uint32_t v[GW][H];
+#pragma unroll
+    for (int q = 0; q < GW; ++q) {
+      const int64_t g = g0 + q * nw;
+      const uint32_t* row = p0t + (size_t)(g < G ? g : 0) * d;
+#pragma unroll
+      for (int h = 0; h < H; ++h) v[q][h] = (h < nh && g < G) ? __ldg(row + ax[h]) ^ flip[h] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < GW; ++q) {
+      const int64_t g = g0 + q * nw;
+      if (g >= G) break;
+      const int64_t p = g * 32 + lane;
+      uint32_t carry = 0, hi = 0;
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        if (h >= nh) break;
+        uint32_t x = v[q][h];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x ^= t;
+        }
+        x ^= carry;
+        carry = __shfl_sync(0xffffffffu, x, 31);
+        const uint32_t half = __brev(warp_transpose32(x, lane));
+        if (h & 1) {
+          if (p < n) pk[(size_t)(h >> 1) * n + p] = ((uint64_t)hi << 32) | half;
+        } else {
+          hi = half;
+        }
       }
     }
   }
@@ -165,7 +189,13 @@ void launch_prefix_keys(const uint32_t* planes, const uint32_t* p0t, int64_t n, 
   const int W32 = (d + 31) / 32;
   if (prefix_top_path(d, K, L) && p0t) {
     const int64_t G = (n + 31) / 32;
-    prefix_sliced_kernel<<<hf_blocks(G * 32, 256, 152 * 16), 256, 0, s>>>(p0t, n, d, K, pi, rbits, pk);
+    const unsigned blocks = hf_blocks(G * 32, 256, 152 * 16);
+    if (K <= 2)
+      prefix_sliced_kernel<4><<<blocks, 256, 0, s>>>(p0t, n, d, K, pi, rbits, pk);
+    else if (K <= 4)
+      prefix_sliced_kernel<8><<<blocks, 256, 0, s>>>(p0t, n, d, K, pi, rbits, pk);
+    else
+      prefix_sliced_kernel<16><<<blocks, 256, 0, s>>>(p0t, n, d, K, pi, rbits, pk);
     hf_after_launch("prefix_sliced_kernel", s);
     return;
   }
