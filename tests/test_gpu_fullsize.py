@@ -229,3 +229,78 @@ def test_tensor_ragged_1m_w64(hf):
     oi, od = O.topk_from_candidates(x, pts, cand, K)
     check_tensor_lists(x, gi.cpu().numpy()[pts], gd.cpu().numpy()[pts], oi, owners=pts, cand=cand)
     G.close()
+
+
+def test_sketch_sampled_graph_rows(full):
+    """The sketch form (384-bit sketches, k2 = 60) on the full-size forest:
+    sampled rows against the oracle's Hamming top-k2 and exact top-k of their
+    window candidates (from the checked orders). Rows whose point or a
+    candidate holds a sketch bit within the FP32 bound of its decision are
+    checked for validity only."""
+    from oracle import sketch as OS
+    x, G = full["x"], full["G"]
+    R = S.sketch_projection(384, D, seed=S.SEED_SKETCH)
+    G.set_sketch(torch.from_numpy(R).cuda())
+    G.set_option("mode", 3)
+    G.set_option("sketch_k2", 60)
+    gi, gd = G.knn_graph(K, W)
+    G.set_option("mode", 0)
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    skg = G.sketches()
+    rng = np.random.default_rng(S.SEED_SAMPLE + 3)
+    pts = np.sort(rng.choice(N, 800, replace=False))
+    cand = window_rows(full["orders"], pts, W)
+    need = np.unique(np.concatenate([pts, cand[cand >= 0]]))
+    dots = OS.sketch_dots(x[need], R)
+    xb, rb = O.budget.bf16(x[need]), O.budget.bf16(R)
+    amb = np.abs(dots) <= D * 2.0 ** -24 * (np.abs(xb) @ np.abs(rb).T)
+    sk = np.zeros((N, 6), np.uint64)
+    sk[need] = OS.pack_bits(dots > 0)
+    flipped = np.zeros(N, bool)
+    bits_g = np.unpackbits(skg[need].view(np.uint8), axis=1, bitorder="little").astype(bool)
+    assert not ((bits_g != (dots > 0)) & ~amb).any(), "sketch bits differ outside the FP32 bound"
+    flipped[need] = (bits_g != (dots > 0)).any(axis=1)
+    c2 = OS.top_k2_by_hamming(sk, pts, cand, 60)
+    oi, od = O.topk_from_candidates(x, pts, c2, K)
+    touched = flipped[pts] | np.array([flipped[c[c >= 0]].any() for c in cand])
+    strict = ~touched
+    assert strict.mean() > 0.5
+    check_lists(x, gi[pts][strict], gd[pts][strict], oi[strict], od[strict], owners=pts[strict], cand=cand[strict],
+                min_equal=0.99)
+
+
+def test_batched_workload_equals_independent(hf):
+    """The batched workload at full size (64 sets, 2.8M points, the forms and
+    windows the bench's tuner picks): every row of every set equals the same
+    set built and graphed alone; two small sets also against the oracle."""
+    sets = S.batched_sets(64)
+    plan = {64: (1, 16, 256), 128: (1, 16, 256), 384: (1, 16, 384), 768: (2, 32, 512)}  # form, slots, w
+    k, T2 = 10, 16
+    for d, (form, slots, w) in plan.items():
+        idx = [i for i, x in enumerate(sets) if x.shape[1] == d]
+        off = np.zeros(len(idx) + 1, np.int64)
+        off[1:] = np.cumsum([sets[i].shape[0] for i in idx])
+        G = hf.build_segmented(torch.from_numpy(np.concatenate([sets[i] for i in idx])).cuda(), off, T=T2, seed=3)
+        G.set_option("mode", form)
+        G.set_option("tensor_slack", slots - k)
+        gi, gd = G.knn_graph(k, w)
+        gi, gd = gi.cpu().numpy().astype(np.int64), gd.cpu().numpy()
+        G.close()
+        for j, i in enumerate(idx):
+            a, b = off[j], off[j + 1]
+            H = hf.build(torch.from_numpy(sets[i]).cuda(), T=T2, seed=3)
+            H.set_option("mode", form)
+            H.set_option("tensor_slack", slots - k)
+            hi_, hd_ = H.knn_graph(k, w)
+            H.close()
+            hi_ = hi_.cpu().numpy().astype(np.int64)
+            assert np.array_equal(gi[a:b], np.where(hi_ >= 0, hi_ + a, -1)), f"set {i} (d={d}): lists"
+            assert np.array_equal(gd[a:b], hd_.cpu().numpy()), f"set {i} (d={d}): distances"
+        small = min(range(len(idx)), key=lambda j: off[j + 1] - off[j])
+        a, b = off[small], off[small + 1]
+        x = sets[idx[small]]
+        F = O.Forest(x, T=T2, bits=8, seed=3)
+        oi, _ = O.knn_graph(F, k, w)
+        li = np.where(gi[a:b] >= 0, gi[a:b] - a, -1)
+        check_tensor_lists(x, li, gd[a:b], oi, owners=np.arange(b - a), cand=O.candidate_sets(F, w),
+                           min_hit=0.98 if form == 1 else 0.93)
