@@ -425,8 +425,10 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
  * float), [7] re-rank (modes 1, 2), [8] the form the last hf_knn_graph ran
  * (0 = plain float32 window kernel, 1 = BF16 tensor-core Gram bands, 2 = FP8
  * e4m3 Gram bands, 3 = sketch form), so a caller that asked for a tensor form can see whether
- * it fell back, [9] the part of [4] spent gathering each tree's rows into its
- * order (tensor forms), [10..11] reserved (0). Writes min(cap, 12).
+ * it fell back, [9] the time spent gathering each tree's rows into its
+ * order (tensor forms; on a second stream, overlapping the previous tree's
+ * Gram band, so it is not a part of [4]), [10] the Gram band launches alone
+ * (tensor forms), [11] reserved (0). Writes min(cap, 12).
  */
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
 

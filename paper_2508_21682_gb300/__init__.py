@@ -354,7 +354,7 @@ class Forest:
         t = np.zeros(12, np.float32)
         lib().hf_get_timings(self._h, t.ctypes.data, 12)
         names = ["quantize", "keys", "sort", "tie_fixup", "window_merge", "search", "build_launches", "rerank",
-                 "graph_form", "gather"]
+                 "graph_form", "gather", "gram"]
         return dict(zip(names, t.tolist()))
 
     # ---- inspection --------------------------------------------------------

@@ -166,6 +166,10 @@ void destroy(hf_forest* f, cudaStream_t s) {
   dfree(f->plan_ld, s);
   dfree(f->plan_xs, s);
   dfree(f->plan_ms, s);
+  if (f->side) {
+    cudaStreamSynchronize(s);  // the stream-ordered frees above run before the side stream goes
+    cudaStreamDestroy(f->side);
+  }
   delete f;
 }
 
@@ -212,11 +216,12 @@ struct Timer {
   std::vector<cudaEvent_t> events;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[HF_NTIMINGS];
   explicit Timer(hf_forest* ff, cudaStream_t ss) : f(ff), s(ss) {}
-  cudaEvent_t mark() {
+  cudaEvent_t mark() { return mark_on(s); }
+  cudaEvent_t mark_on(cudaStream_t st) {
     cudaEvent_t e = nullptr;
     if (f->timing && cudaEventCreate(&e) == cudaSuccess) {
       events.push_back(e);
-      cudaEventRecord(e, s);
+      cudaEventRecord(e, st);
     }
     return e;
   }
@@ -586,16 +591,21 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   if (tensor && kp > 32) return HF_ENOTIMPL;  // tensor lists hold at most 32 entries
   uint32_t* li = nullptr;
   float* ldd = nullptr;
-  void* xs = nullptr;  // tensor forms: one tree's rows in its order
-  float2* ms = nullptr;
+  // tensor forms: two trees' rows in their orders (the next tree's rows are
+  // gathered on a side stream while the Gram band of this tree runs)
+  void* xs[2] = {nullptr, nullptr};
+  float2* ms[2] = {nullptr, nullptr};
   uint16_t* pw = nullptr;     // per-point windows of one tree
   int32_t* tile_w = nullptr;  // per-tile windows of one tree
   cudaError_t e = dalloc(&li, (size_t)n * kp, s);
   if (e == cudaSuccess) e = dalloc(&ldd, (size_t)n * kp, s);
   if (e == cudaSuccess && budget) e = dalloc(&pw, (size_t)n, s);
   if (e == cudaSuccess && budget) e = dalloc(&tile_w, (size_t)(n + 127) / 128, s);
-  if (e == cudaSuccess && tensor) e = dalloc_bytes(&xs, (size_t)n * gram_row_bytes(f->d, form), s);
-  if (e == cudaSuccess && tensor) e = dalloc(&ms, (size_t)n, s);
+  for (int b = 0; b < (T_use > 1 ? 2 : 1) && tensor; ++b) {
+    if (e == cudaSuccess) e = dalloc_bytes(&xs[b], (size_t)n * gram_row_bytes(f->d, form), s);
+    if (e == cudaSuccess) e = dalloc(&ms[b], (size_t)n, s);
+  }
+  if (e == cudaSuccess && tensor && !f->side) e = cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking);
   if (e == cudaSuccess && tensor && f->xform != form) {
     dfree(f->xb, s);
     dfree(f->xmeta, s);
@@ -607,11 +617,17 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
       f->xform = form;
     }
   }
+  cudaEvent_t ev[5] = {};  // gathered[2], band done[2], side stream idle
+  for (int i = 0; i < 5 && e == cudaSuccess && tensor; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
     dfree(li, s);
     dfree(ldd, s);
-    dfree(xs, s);
-    dfree(ms, s);
+    for (int b = 0; b < 2; ++b) {
+      dfree(xs[b], s);
+      dfree(ms[b], s);
+    }
     dfree(pw, s);
     dfree(tile_w, s);
     return map_cuda(e);
@@ -620,20 +636,47 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   cudaEvent_t a0 = tm.mark();
   launch_list_init(li, ldd, n * kp, s);
   int rc = HF_OK;
+  cudaStream_t side = f->side;
+  auto gather = [&](int t) {  // tree t's rows into buffer t % 2, on the side stream
+    const int b = T_use > 1 ? (t & 1) : 0;
+    cudaEvent_t g0 = tm.mark_on(side);
+    launch_gather_rows(f->xb, f->xmeta, form, n, f->d, f->sigma + (size_t)t * n, xs[b], ms[b], side);
+    cudaEvent_t g1 = tm.mark_on(side);
+    tm.span(9, g0, g1);
+    cudaEventRecord(ev[b], side);
+  };
+  if (tensor) {
+    cudaEventRecord(ev[4], s);  // operands prepared, lists initialised
+    cudaStreamWaitEvent(side, ev[4], 0);
+    gather(0);
+  }
   for (int t = 0; t < T_use && rc == HF_OK; ++t) {
     if (tensor) {
+      const int b = T_use > 1 ? (t & 1) : 0;
       const uint32_t* sig = f->sigma + (size_t)t * n;
       if (budget) launch_tree_budget(sig, n, t, wpt, tpt, pw, tile_w, s);
-      cudaEvent_t g0 = tm.mark();
-      launch_gather_rows(f->xb, f->xmeta, form, n, f->d, sig, xs, ms, s);
-      cudaEvent_t g1 = tm.mark();
-      tm.span(9, g0, g1);
-      rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs, ms, s, f->seg, f->seg_off);
+      cudaStreamWaitEvent(s, ev[b], 0);
+      cudaEvent_t m0 = tm.mark();
+      rc = launch_gram_window(form, n, f->d, sig, w, tile_w, pw, kp, li, ldd, f->err, xs[b], ms[b], s, f->seg,
+                              f->seg_off);
+      cudaEvent_t m1 = tm.mark();
+      tm.span(10, m0, m1);
+      cudaEventRecord(ev[2 + b], s);
+      if (rc == HF_OK && t + 1 < T_use) {
+        // buffer (t + 1) % 2 was read by tree t - 1's band
+        if (t >= 1) cudaStreamWaitEvent(side, ev[2 + ((t + 1) & 1)], 0);
+        gather(t + 1);
+      }
     } else if (sketchf) {
       rc = launch_window_hamming(reinterpret_cast<const uint32_t*>(f->sketch), n, f->sketch_bits / 32,
                                  f->sigma + (size_t)t * n, w, kp, li, ldd, s, f->seg, f->seg_off);
     } else
       rc = launch_window_graph(f->x, n, f->d, f->sigma + (size_t)t * n, w, kp, li, ldd, s, f->seg, f->seg_off);
+  }
+  if (tensor) {
+    // nothing of the side stream may outlive the buffers freed on s
+    cudaEventRecord(ev[4], side);
+    cudaStreamWaitEvent(s, ev[4], 0);
   }
   cudaEvent_t a1 = tm.mark();
   if (rc == HF_OK && (tensor || sketchf))
@@ -662,11 +705,16 @@ int knn_graph_impl(hf_forest* f, int32_t k, int32_t w, const int32_t* wpt, const
   int rc2 = finish(f, s);
   if (rc == HF_OK) rc = rc2;
   f->timings[9] = 0.f;
-  if (rc == HF_OK) tm.collect({4, 7, 9});
+  f->timings[10] = 0.f;
+  if (rc == HF_OK) tm.collect({4, 7, 9, 10});
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
   dfree(li, s);
   dfree(ldd, s);
-  dfree(xs, s);
-  dfree(ms, s);
+  for (int b = 0; b < 2; ++b) {
+    dfree(xs[b], s);
+    dfree(ms[b], s);
+  }
   dfree(pw, s);
   dfree(tile_w, s);
   return rc;

@@ -106,6 +106,7 @@ struct hf_forest {
   int sketch_k2 = 60;     // candidates kept by Hamming distance (mode 3)
   int expand_h = 2;       // master-order neighbours per survivor (mode 3 search)
   int timing = 1;
+  cudaStream_t side = nullptr;  // second stream of the tensor forms' row gathers
 
   float timings[HF_NTIMINGS] = {0};
 };
