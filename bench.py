@@ -223,6 +223,17 @@ def exact_knn_gpu(xd, rows_d, k, exclude=None, chunk=None):
     return np.array(out)
 
 
+def dist_error(xd, rows_t, idx, dist):
+    """Largest relative error of returned float32 distances against float64
+    recomputations (exact coordinate differences) over the given rows."""
+    ok = idx >= 0
+    j = idx.clamp(min=0).long()
+    diff = xd[j].double() - xd[rows_t].double()[:, None, :]
+    true = (diff * diff).sum(-1)
+    err = ((dist.double() - true).abs() / true.clamp(min=1e-30))[ok]
+    return float(err.max().item()) if err.numel() else 0.0
+
+
 def recall(found, exact):
     k = exact.shape[1]
     return float(np.mean([len(set(a[a >= 0].tolist()) & set(b.tolist())) / k for a, b in zip(found, exact)]))
@@ -321,6 +332,7 @@ def run_ours(a):
         step()  # the default mode's graph again for its own recall
         torch.cuda.synchronize()
     rec = recall(gi.cpu().numpy()[rows], ex)
+    dist_err = dist_error(xd, rows_t, gi[rows_t], gd[rows_t])
     qs = min(500, a.nq)
     exq = exact_knn_gpu(xd, qd[:qs], k)
     rec_q = recall(si[:qs].cpu().numpy(), exq)
@@ -387,6 +399,7 @@ def run_ours(a):
                        "parallelism": f"replicas x{ws}"},
             "recall_at_k": rec,
             "at_metric_recall": bool(rec >= 0.8),
+            "max_rel_dist_err_vs_f64": dist_err,
             "keys_sort_hbm": keys_sort_hbm(a, ph),
             "recall_sample": int(len(rows)),
             "search_recall_at_k": rec_q,
@@ -872,7 +885,9 @@ def batched_form(a, hf, dev):
             rows = np.unique(np.linspace(a0, a1 - 1, num=min(32, a1 - a0)).astype(np.int64))
             ei, _ = G.exact_knn_rows(rows, k)
             hit = sum(len(set(x[x >= 0]) & set(y[y >= 0])) for x, y in zip(gi[rows], ei))
-            per_set[i] = {"n": a1 - a0, "d": g["d"], "recall_at_k": hit / max(1, int((ei >= 0).sum()))}
+            rt = torch.from_numpy(rows).to(dev)
+            per_set[i] = {"n": a1 - a0, "d": g["d"], "recall_at_k": hit / max(1, int((ei >= 0).sum())),
+                          "max_rel_dist_err_vs_f64": dist_error(g["X"], rt, g["oi"][rt], g["od"][rt])}
     for G in forests:
         G.close()
     graph.close()
@@ -911,6 +926,7 @@ def batched_form(a, hf, dev):
         "speedup_vs_one_at_a_time": loop_ms / step_ms,
         "recall_target": a.batched_recall,
         "recall_at_k_mean": float(np.mean([p["recall_at_k"] for p in per_set])),
+        "max_rel_dist_err_vs_f64": float(max(p["max_rel_dist_err_vs_f64"] for p in per_set)),
         "per_set": per_set,
     }
 

@@ -121,11 +121,14 @@ int hf_build_opts(const float* points, int64_t n, int32_t d, int32_t T, int32_t 
                   uint64_t seed, const char* options, void* stream, hf_forest** out);
 
 /*
- * hf_knn_graph -- approximate kNN graph (Algorithm 2 first stage and final
- * selection; the sketch stage is not part of this path).
+ * hf_knn_graph -- approximate kNN graph (Algorithm 2; its second stage, the
+ * sketch filter, runs in mode 3 only).
  * For every point, the candidates are the points within w positions of it in
  * any tree's order; the result is the k nearest candidates by float32 squared
- * distance, ascending by (distance, index).
+ * distance, ascending by (distance, index). Every form ends with one re-rank
+ * of each point's kept candidates: the returned distances are float32 exact-
+ * difference sums whose lane partials are added by a butterfly (relative
+ * error below (4 ceil(d / 128) + 7) 2^-24, 1.1e-6 at d = 384).
  * k        : 1 <= k <= HF_MAX_K.
  * w        : window half-width, w >= 1.
  * out_idx  : n x k int32 (row i = neighbours of point i); -1 in unfilled slots.
@@ -388,8 +391,10 @@ const char* hf_status_string(int status);
 
 /*
  * hf_set_option -- per-forest run-time options for later calls:
- *   mode=0  plain float32 window distances (default); w <= HF_PLAIN_MAX_W
- *           (HF_ENOTIMPL beyond);
+ *   mode=0  plain float32 window distances (default), each point keeping its
+ *           best window_list_pitch(k) candidates by their sequential-sum
+ *           distance before the re-rank; w <= HF_PLAIN_MAX_W (HF_ENOTIMPL
+ *           beyond);
  *   mode=1  tensor-core window distances: BF16 Gram bands (tcgen05, FP32
  *           accumulation) estimate every candidate's distance, each point
  *           keeps its best k + slack (rounded up to 16 or 32; see
@@ -422,7 +427,7 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
  * [0] quantize, [1] keys, [2] sort (with the small-run fix-up), [3] big-run
  * fix-up, [4] window distances + merge (all trees; the Gram kernels in mode
  * 1), [5] search, [6] number of kernel launches of the last build (as a
- * float), [7] re-rank (modes 1, 2), [8] the form the last hf_knn_graph ran
+ * float), [7] re-rank (every form), [8] the form the last hf_knn_graph ran
  * (0 = plain float32 window kernel, 1 = BF16 tensor-core Gram bands, 2 = FP8
  * e4m3 Gram bands, 3 = sketch form), so a caller that asked for a tensor form can see whether
  * it fell back, [9] the time spent gathering each tree's rows into its
