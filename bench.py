@@ -304,6 +304,30 @@ def run_ours(a):
     else:
         roof = window_roofline(a, launch_ms)
 
+    # end to end through the C ABI with pinned host buffers, right after the
+    # timed region (the same device state as the timed steps)
+    xh = torch.from_numpy(x).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    gih = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    gdh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    sih = torch.empty((a.nq, k), dtype=torch.int32).pin_memory()
+    sdh = torch.empty((a.nq, k), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for i in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G = hf.build(xh, T=T, bits=a.bits, seed=3)
+        if a.mode != "plain":
+            G.set_option("mode", MODES[a.mode])
+            G.set_option("tensor_slack", a.tensor_slack)
+        G.knn_graph(k, w, gih, gdh)
+        G.search(qh, k, a.search_w, sih, sdh)
+        G.close()
+        torch.cuda.synchronize()
+        if i:  # first one is a warm-up
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms) if e2e_ms else float("nan"), dist, dev)
+
     # plain float32 mode beside it (outside the timed region)
     plain = None
     if a.mode != "plain" and a.plain_steps > 0:
@@ -347,28 +371,6 @@ def run_ours(a):
     if not a.no_batched and rank == 0:
         batched = batched_form(a, hf, dev)
 
-    # end to end through the C ABI with pinned host buffers
-    xh = torch.from_numpy(x).pin_memory()
-    qh = torch.from_numpy(q).pin_memory()
-    gih = torch.empty((n, k), dtype=torch.int32).pin_memory()
-    gdh = torch.empty((n, k), dtype=torch.float32).pin_memory()
-    sih = torch.empty((a.nq, k), dtype=torch.int32).pin_memory()
-    sdh = torch.empty((a.nq, k), dtype=torch.float32).pin_memory()
-    e2e_ms = []
-    for i in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G = hf.build(xh, T=T, bits=a.bits, seed=3)
-        if a.mode != "plain":
-            G.set_option("mode", MODES[a.mode])
-            G.set_option("tensor_slack", a.tensor_slack)
-        G.knn_graph(k, w, gih, gdh)
-        G.search(qh, k, a.search_w, sih, sdh)
-        G.close()
-        torch.cuda.synchronize()
-        if i:  # first one is a warm-up
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_step = max_over_ranks(statistics.mean(e2e_ms) if e2e_ms else float("nan"), dist, dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
