@@ -668,13 +668,23 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __gr
             if (F8) ss = *reinterpret_cast<const float4*>(se.sc + (c0 - u0) + 4 * q4);
             const float nv[4] = {nn.x, nn.y, nn.z, nn.w};
             const float sv[4] = {ss.x, ss.y, ss.z, ss.w};
+            // two columns per packed FP32 pair instruction (fma.rn.f32x2,
+            // sub.rn.f32x2: each lane of the pair rounds as the scalar form)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < 4; e += 2) {
               const int jj = 4 * q4 + e;
-              const float dot = __uint_as_float(v[jj]);
-              const float part = F8 ? fmaf(-c2 * sv[e], dot, nv[e]) : fmaf(-2.0f, dot, nv[e]);
-              v[jj] = __float_as_uint(part);  // the partial estimate replaces the dot product
-              miss = __funnelshift_l(__float_as_uint(ti - part), miss, 1);
+              const float m0 = F8 ? -c2 * sv[e] : -2.0f, m1 = F8 ? -c2 * sv[e + 1] : -2.0f;
+              uint32_t p0, p1, d0, d1;
+              asm("{\n .reg .b64 a, m, nn, t, p, dd;\n"
+                  " mov.b64 a, {%4, %5};\n mov.b64 m, {%6, %7};\n mov.b64 nn, {%8, %9};\n mov.b64 t, {%10, %10};\n"
+                  " fma.rn.f32x2 p, a, m, nn;\n sub.rn.f32x2 dd, t, p;\n"
+                  " mov.b64 {%0, %1}, p;\n mov.b64 {%2, %3}, dd;\n}"
+                  : "=r"(p0), "=r"(p1), "=r"(d0), "=r"(d1)
+                  : "r"(v[jj]), "r"(v[jj + 1]), "f"(m0), "f"(m1), "f"(nv[e]), "f"(nv[e + 1]), "f"(ti));
+              v[jj] = p0;  // the partial estimates replace the dot products
+              v[jj + 1] = p1;
+              miss = __funnelshift_l(d0, miss, 1);
+              miss = __funnelshift_l(d1, miss, 1);
             }
           }
           uint32_t hm = __brev(~miss) & wm;
