@@ -254,16 +254,16 @@ struct GramArgs {
 // own rows positions [s, s + 128).
 //   warp 0      TMA producer (one lane): per K chunk of a unit, boxes of 32
 //               rows x 128 bytes into the B ring (128-byte swizzle, rows
-//               outside the matrix zero-filled); per tile with several
-//               units, the own rows into the resident A region, chunk kc
-//               once the previous tile's last MMA reading it has completed;
+//               outside the matrix zero-filled);
 //   warp 1      MMA issuer (one lane): per unit, all K chunks into one of two
 //               tensor-memory accumulators (256 columns each); it also owns
 //               the tensor-memory allocation;
 //   warp 2      prep: per unit, the (norm, scale, id) of its columns (and, for
 //               the first unit, of the tile's own rows) into one of NSLOT
 //               slots;
-//   warp 3      idle;
+//   warp 3      A producer (one lane): per tile with several units, the own
+//               rows into the resident A region, chunk kc once the previous
+//               tile's last MMA reading it has completed;
 //   warps 4..11 epilogue: a warp owns tensor-memory lanes 32 (warp % 4) ..
 //               + 31 (tile rows) and, in half h = (warp - 4) / 4, the
 //               32-column chunks of parity h.
@@ -278,6 +278,7 @@ constexpr int XE = 16;             // list entries handed over per exchange roun
 constexpr int TW = 0;              // TMA producer warp
 constexpr int MW = 1;              // MMA warp
 constexpr int PW = 2;              // prep warp
+constexpr int AW = 3;              // A (own rows) producer warp
 constexpr int EW0 = 4;             // first epilogue warp
 constexpr int PT = (EW0 + 8) * 32;
 constexpr uint32_t TMEM_ALL = 512; // two accumulators of 256 columns
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __gr
   if (warp == TW) {
     // ---------------- TMA producer (one lane)
     if (lane == 0) {
-      uint32_t it = 0, auses = 0;
+      uint32_t it = 0;
       bool ok = true;
       const uint32_t chunk_box = (uint32_t)BOX_ROWS * 128u;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -454,20 +455,8 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __gr
           const int nj = min(SLOT_COLS, g.ncol - SLOT_COLS * j);
           const int nbox = (nj + BOX_ROWS - 1) / BOX_ROWS;
           const int y0 = (int)(c_lo + (int64_t)SLOT_COLS * j);
-          const bool useA = g.J > 1 && j == 0;
           for (int kc = 0; kc < nk; ++kc, ++it) {
             const int x = kc * a.elem_per_chunk;
-            if (useA) {
-              if (!pwait(&S.aempty[kc], (auses & 1) ^ 1, lim, abort, a.err)) {
-                ok = false;
-                break;
-              }
-              mbar_arrive_expect_tx(&S.afull[kc], (uint32_t)GB * 128u);
-              const uint32_t d0 = smem_u32(aregion + (size_t)kc * GB * 128);
-#pragma unroll
-              for (int b = 0; b < GB / BOX_ROWS; ++b)
-                tma_load_2d(d0 + (uint32_t)b * chunk_box, &xmap, x, (int)s + b * BOX_ROWS, &S.afull[kc]);
-            }
             const int st = it % stages;
             if (!pwait(&S.empty[st], ((it / stages) & 1) ^ 1, lim, abort, a.err)) {
               ok = false;
@@ -477,8 +466,35 @@ __global__ void __launch_bounds__(PT, 1) gram_band_kernel(GramArgs a, const __gr
             const uint32_t d0 = smem_u32(bring + (size_t)st * a.b_stage_bytes);
             for (int b = 0; b < nbox; ++b) tma_load_2d(d0 + (uint32_t)b * chunk_box, &xmap, x, y0 + b * BOX_ROWS, &S.full[st]);
           }
-          if (useA) ++auses;
         }
+      }
+    }
+    __syncwarp();
+  } else if (warp == AW) {
+    // ---------------- A producer (one lane): the tile's own rows, chunk kc
+    // as soon as the previous tile's last MMA reading chunk kc has completed
+    // (a thread of its own, so the B ring of the next tile never waits for it)
+    if (lane == 0) {
+      uint32_t auses = 0;
+      bool ok = true;
+      const uint32_t chunk_box = (uint32_t)BOX_ROWS * 128u;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileGeom g = tile_geom(a, t);
+        if (g.J <= 1) continue;
+        const int64_t s = t * GB;
+        for (int kc = 0; kc < nk; ++kc) {
+          if (!pwait(&S.aempty[kc], (auses & 1) ^ 1, lim, abort, a.err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.afull[kc], (uint32_t)GB * 128u);
+          const uint32_t d0 = smem_u32(aregion + (size_t)kc * GB * 128);
+#pragma unroll
+          for (int b = 0; b < GB / BOX_ROWS; ++b)
+            tma_load_2d(d0 + (uint32_t)b * chunk_box, &xmap, kc * a.elem_per_chunk, (int)s + b * BOX_ROWS,
+                        &S.afull[kc]);
+        }
+        ++auses;
       }
     }
     __syncwarp();
