@@ -14,13 +14,17 @@ mixture queries with N(0, 0.05^2) noise. The paper measured on GOOAQ
 The default form is the tensor mode: window distances as BF16 Gram tiles on
 the tensor cores (tcgen05) keeping k + 1 candidates per point, then an exact
 float32 re-rank; `--mode plain` runs the all-float32 window kernel instead
-(two plain steps are also timed beside the default, for comparison).
+(one plain step is also timed beside the default, for comparison).
 
 Prints one JSON line (rank 0). `value` = points / s of the device-resident
 step; `e2e` = the same through the C ABI with pinned host buffers (copies in
 the timed region); `roofline` for the dominant kernel (the Gram kernel in
 tensor mode, the window kernel in plain mode); `cpu_baseline` = the CPU oracle
-on a bounded sample.
+on a bounded sample (and the tiny configuration in full). Blocks measured
+after the timed region: `plain_f32`, `learned` (per-point budgets), `sketch`
+(the paper's second stage), `batched` (64 independent sets, CUDA graph,
+autotuner) and `tiny` (20,000 x 16). `--workload c3` runs the large search
+workload instead (23M x 384, T = 160, 10k queries) and prints its own line.
 
 --impl reference times the CPU oracle itself (the only reference this
 project has: the paper ships no code) on a bounded sample per step.
@@ -87,6 +91,7 @@ def args():
     p.add_argument("--train-steps", type=int, default=3000)
     p.add_argument("--no-sketch", action="store_true", help="skip the sketch-form comparison")
     p.add_argument("--no-batched", action="store_true", help="skip the batched form (64 independent sets)")
+    p.add_argument("--no-tiny", action="store_true", help="skip the tiny configuration (20,000 x 16)")
     p.add_argument("--batched-sets", type=int, default=64)
     p.add_argument("--batched-recall", type=float, default=0.8, help="autotuner recall target per d group")
     p.add_argument("--batched-steps", type=int, default=3)
@@ -370,6 +375,9 @@ def run_ours(a):
     batched = None
     if not a.no_batched and rank == 0:
         batched = batched_form(a, hf, dev)
+    tiny = None
+    if not a.no_tiny and rank == 0:
+        tiny = tiny_form(a, hf, dev)
 
 
     cpu = None
@@ -412,6 +420,7 @@ def run_ours(a):
             "learned": learned,
             "sketch": sketch,
             "batched": batched,
+            "tiny": tiny,
             "e2e": {"value": job_value(ws, n, e2e_step), "unit": "points/s",
                     "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
@@ -595,8 +604,19 @@ def cpu_baseline(a):
     val, wall = oracle_parallel(a, cores, n_s, T_s)
     p8 = min(8, cores)
     val8, wall8 = oracle_parallel(a, p8, n_s, T_s) if p8 != cores else (val, wall)
+    # the tiny configuration in full (20,000 x 16, T = 8, w = 16, k = 10),
+    # in this process with numpy's own threads
+    import synthdata as S
+    import oracle as O
+    xt = S.unit_gaussian(20_000, 16, seed=S.SEED_DATA)
+    t0 = time.perf_counter()
+    F = O.Forest(xt, T=8, bits=a.bits, seed=S.SEED_FOREST)
+    O.knn_graph(F, 10, 16)
+    tiny_s = time.perf_counter() - t0
     return {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
             "cpu": cpu_model(), "value_8": val8, "cores_8": p8,
+            "tiny_full": {"workload": "20,000 x 16 unit Gaussian, T=8, b=8, w=16, k=10 (build + graph, in full)",
+                          "s": tiny_s, "value": 20_000 / tiny_s, "unit": "points/s"},
             "sample": f"numpy oracle (float64), one single-threaded process per core, each on its own {n_s} points "
                       f"of the same mixture with {T_s} of {a.T} trees, w={a.w}, k={a.k}, queries pro rata "
                       f"(w={a.search_w}); {wall:.1f} s wall on {cores} cores, {wall8:.1f} s on {p8}; "
@@ -794,6 +814,44 @@ def sketch_form(a, hf, xd, qd, rows, ex, exq, qs, dev):
             search[form].update({"k2": k2s, "h": hs})
     out["search"] = search
     G.close()
+    return out
+
+
+def tiny_form(a, hf, dev):
+    """The tiny configuration: n = 20,000, d = 16 unit Gaussian rows, T = 8,
+    b = 8, w = 16, k = 10. Everything fits in L2, so the figure is absolute
+    time (launch- and latency-bound), not a roofline fraction. Plain float32
+    form (the configuration's distances) and the BF16 Gram form, each the
+    median of 9 steps (build + graph, CUDA events), with recall@10 against
+    exact brute force of all points."""
+    import torch
+    import synthdata as S
+
+    n, d, T, w, k = 20_000, 16, 8, 16, 10
+    xd = torch.from_numpy(S.unit_gaussian(n, d, seed=S.SEED_DATA)).to(dev)
+    rows = np.arange(n)
+    ex = exact_knn_gpu(xd, xd, k, exclude=torch.arange(n, device=dev))
+    gi = torch.empty((n, k), dtype=torch.int32, device=dev)
+    gd = torch.empty((n, k), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    out = {"workload": f"n={n}, d={d} unit Gaussian, T={T}, b={a.bits}, w={w}, k={k}"}
+    for form, mode in (("plain", 0), ("tensor", 1)):
+        ms = []
+        for i in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            G = hf.build(xd, T=T, bits=a.bits, seed=S.SEED_FOREST)
+            G.set_option("mode", mode)
+            G.knn_graph(k, w, gi, gd)
+            G.close()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            if i:
+                ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        out[form] = {"us_per_step": med * 1e3, "value": n / (med * 1e-3), "unit": "points/s",
+                     "recall_at_k": recall(gi.cpu().numpy()[rows], ex)}
     return out
 
 
