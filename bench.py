@@ -53,7 +53,7 @@ MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
 WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "cd0725673dcf443f", "file": "window.cu"}   # w = 32
-GRAM_TRAFFIC = {"bytes_per_point": 1131, "source_sha": "8847a300cfccd5b2", "file": "gram.cu"}     # w = 512
+GRAM_TRAFFIC = {"bytes_per_point": 1132, "source_sha": "47427dc25b29ab93", "file": "gram.cu"}     # w = 512
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
