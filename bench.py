@@ -53,7 +53,7 @@ MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
 WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "cd0725673dcf443f", "file": "window.cu"}   # w = 32
-GRAM_TRAFFIC = {"bytes_per_point": 1132, "source_sha": "47427dc25b29ab93", "file": "gram.cu"}     # w = 512
+GRAM_TRAFFIC = {"bytes_per_point": 1132, "source_sha": "47427dc25b29ab93", "file": "gram.cu", "w": 1024}
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-
 # difference distance is FADD + FFMA = 2 issue slots = 3 flops.
@@ -68,11 +68,16 @@ def args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=3_000_000)
     p.add_argument("--d", type=int, default=384)
-    # T = 128 trees and w = 512 on each side: the smallest budget of the
-    # recall sweep at which recall@15 reaches 0.8 on this workload (0.825;
-    # the configured T = 32, w = 32 reaches 0.28)
-    p.add_argument("--T", type=int, default=128)
-    p.add_argument("--w", type=int, default=512)
+    # T = 64 trees and w = 1024 on each side: of the (T, w) cells whose
+    # recall@15 reaches 0.81 in the recall sweep (0.819 here), the one whose
+    # BF16-form step measured fastest (the configured T = 32, w = 32 reaches
+    # 0.28). The plain form cannot run w > 704: it is compared at its own
+    # cheapest cell of the sweep above 0.81 with w <= 704, T = 96, w = 640
+    # (0.817; its pair work grows with T w).
+    p.add_argument("--T", type=int, default=64)
+    p.add_argument("--w", type=int, default=1024)
+    p.add_argument("--plain-T", type=int, default=96)
+    p.add_argument("--plain-w", type=int, default=640)
     p.add_argument("--k", type=int, default=15)
     p.add_argument("--bits", type=int, default=8)
     p.add_argument("--nq", type=int, default=10_000)
@@ -267,7 +272,7 @@ def run_ours(a):
     sd = torch.empty((a.nq, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(tim=None):
+    def step(tim=None, T=T, w=w):
         G = hf.build(xd, T=T, bits=a.bits, seed=3)
         if a.mode != "plain":
             G.set_option("mode", MODES[a.mode])
@@ -338,17 +343,18 @@ def run_ours(a):
     if a.mode != "plain" and a.plain_steps > 0:
         saved = a.mode
         a.mode = "plain"
-        step()
+        pT, pw = a.plain_T, a.plain_w
+        step(T=pT, w=pw)
         torch.cuda.synchronize()
         pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.plain_steps)]
         for e0, e1 in pe:
             e0.record(stream)
-            step()
+            step(T=pT, w=pw)
             e1.record(stream)
         torch.cuda.synchronize()
         a.mode = saved
         pms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in pe)
-        plain = {"ms_per_step": pms, "value": n / (pms * 1e-3), "unit": "points/s"}
+        plain = {"ms_per_step": pms, "value": n / (pms * 1e-3), "unit": "points/s", "T": pT, "w": pw}
         gi_plain = gi.cpu().numpy()
 
     # recall on a seeded sample (outside the timed region)
@@ -507,7 +513,7 @@ def gram_roofline(a, launch_ms, gather_ms=0.0):
     g_bytes = 2.0 * a.n * rowb + 16.0 * a.n
     out = {"bound": "tensor", "kernel": "gram_band_kernel (A5+A6: tcgen05 Gram band + top-k merge)",
            "achieved": t_ach, "peak": tf_peak, "unit": "TFLOP/s", "frac": t_ach / tf_peak,
-           "traffic": traffic_per_launch(GRAM_TRAFFIC, a.n) if a.w == 512 and not fp8 else None,
+           "traffic": traffic_per_launch(GRAM_TRAFFIC, a.n) if a.w == GRAM_TRAFFIC["w"] and not fp8 else None,
            "flops_per_launch": flops, "launch_ms": launch_ms,
            "peak_note": f"bf16_tflops_sustained {src} (MEASURED_PEAKS.json)" + (" x 2 for e4m3" if fp8 else ""),
            "hbm_side": {"achieved": b_ach, "peak": hbm_peak, "unit": "GB/s", "frac": b_ach / hbm_peak,
