@@ -437,7 +437,9 @@ int hf_set_option(hf_forest* f, const char* key, int64_t value);
  */
 int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap);
 
-/* hf_info -- n, d, T, bits, W (key words), K (prefix words) into out[0..5]. */
+/* hf_info -- n, d, T, bits, W (key words), K (prefix words the sort orders
+ * by), K2 (key words the prefix kernels form per point, K <= K2 <= W), L (top
+ * bit levels those words come from) into out[0..7]; the first `cap` only. */
 int hf_info(const hf_forest* f, int64_t* out, int32_t cap);
 
 /*
@@ -460,6 +462,13 @@ int hf_debug_codes(hf_forest* f, uint8_t* out_codes, void* stream);
 
 /* Full keys of tree t, n x W uint64 (row i = point i, word 0 first). */
 int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream);
+
+/* The first K2 key words of tree t as the build's prefix kernels form them
+ * (hf_info's K2; the sort orders by the first K, the rest settle ties),
+ * K2 x n uint64 WORD-major: word w of point i at out_words[w * n + i]. They
+ * equal the first K2 words of hf_debug_keys; this export checks the prefix
+ * kernels (bit-sliced top level, bit-sliced L levels) on their own. */
+int hf_debug_prefix(hf_forest* f, int32_t tree, uint64_t* out_words, void* stream);
 
 /* Order of tree t: sigma[p] = point at position p, n uint32. */
 int hf_debug_order(hf_forest* f, int32_t tree, uint32_t* out_sigma, void* stream);

@@ -29,7 +29,7 @@ HF_ENOTIMPL = -7
 SYMBOLS = [
     "hf_build", "hf_build_opts", "hf_knn_graph", "hf_search", "hf_free", "hf_status_string",
     "hf_set_option", "hf_get_timings", "hf_info", "hf_tree_params", "hf_debug_codes",
-    "hf_debug_keys", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
+    "hf_debug_keys", "hf_debug_prefix", "hf_debug_order", "hf_debug_locate", "hf_debug_keys_from_codes",
     "hf_launch_count", "hf_search_static", "hf_trim_pool",
     "hf_budget_labels", "hf_knn_graph_budget", "hf_mlp_create", "hf_mlp_free", "hf_mlp_param_count",
     "hf_mlp_get_params", "hf_mlp_set_params", "hf_mlp_predict", "hf_mlp_grads", "hf_mlp_train",
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
         "hf_tree_params": [u64, i32, i32, vp, vp],
         "hf_debug_codes": [vp, vp, vp],
         "hf_debug_keys": [vp, i32, vp, vp],
+        "hf_debug_prefix": [vp, i32, vp, vp],
         "hf_debug_order": [vp, i32, vp, vp],
         "hf_debug_locate": [vp, i32, vp, i64, vp, vp],
         "hf_debug_keys_from_codes": [vp, i64, i32, i32, vp, vp],
@@ -202,9 +203,10 @@ class Forest:
             rc = lib().hf_build_opts(p, n, d, T, bits, seed, options.encode(), st, ctypes.byref(h))
         _check(rc, "hf_build")
         self._h = h
-        info = np.zeros(6, np.int64)
-        lib().hf_info(self._h, info.ctypes.data, 6)
+        info = np.zeros(8, np.int64)
+        lib().hf_info(self._h, info.ctypes.data, 8)
         self.W, self.K = int(info[4]), int(info[5])
+        self.K2, self.L = int(info[6]), int(info[7])
 
     def close(self):
         if getattr(self, "_h", None):
@@ -367,6 +369,14 @@ class Forest:
         out = np.empty((self.n, self.W), np.uint64)
         _check(lib().hf_debug_keys(self._h, tree, out.ctypes.data, None), "hf_debug_keys")
         return out
+
+    def prefix(self, tree: int):
+        """The K2 key words per point that tree `tree`'s sort keys are formed
+        from, as the key kernels compute them: uint64 [n][K2] on the host
+        (the library returns them word-major)."""
+        out = np.empty((self.K2, self.n), np.uint64)
+        _check(lib().hf_debug_prefix(self._h, tree, out.ctypes.data, None), "hf_debug_prefix")
+        return np.ascontiguousarray(out.T)
 
     def order(self, tree: int, out=None):
         """sigma of tree `tree` (position -> point), uint32[n] on the host, or

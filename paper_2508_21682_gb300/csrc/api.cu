@@ -555,8 +555,8 @@ int hf_get_timings(const hf_forest* f, float* out_ms, int32_t cap) {
 
 int hf_info(const hf_forest* f, int64_t* out, int32_t cap) {
   if (!f || !out || cap < 0) return HF_EINVAL;
-  const int64_t v[6] = {f->n, f->d, f->T, f->bits, f->W, f->K};
-  for (int i = 0; i < cap && i < 6; ++i) out[i] = v[i];
+  const int64_t v[8] = {f->n, f->d, f->T, f->bits, f->W, f->K, f->K2, f->L};
+  for (int i = 0; i < cap && i < 8; ++i) out[i] = v[i];
   return HF_OK;
 }
 
@@ -1253,6 +1253,23 @@ int hf_debug_keys(hf_forest* f, int32_t tree, uint64_t* out_keys, void* stream) 
                           f->rbits + (size_t)tree * f->W32, kk, s);
   int rc = HF_OK;
   if (!dev) rc = map_cuda(cudaMemcpyAsync(out_keys, kk, cnt * 8, cudaMemcpyDeviceToHost, s));
+  int rc2 = finish(f, s);
+  if (!dev) dfree(kk, s);
+  return rc ? rc : rc2;
+}
+
+int hf_debug_prefix(hf_forest* f, int32_t tree, uint64_t* out_words, void* stream) {
+  if (!f || !out_words || tree < 0 || tree >= f->T) return HF_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // an earlier call's error was reported by that call
+  const size_t cnt = (size_t)f->n * f->K2;
+  const bool dev = classify(out_words) == 1;
+  uint64_t* kk = dev ? out_words : nullptr;
+  if (!dev && dalloc(&kk, cnt, s) != cudaSuccess) return HF_ENOMEM;
+  launch_prefix_keys(f->planes, f->p0t, f->n, f->d, f->bits, f->K2, f->L, f->pi + (size_t)tree * f->d,
+                     f->rbits + (size_t)tree * f->W32, kk, s);
+  int rc = HF_OK;
+  if (!dev) rc = map_cuda(cudaMemcpyAsync(out_words, kk, cnt * 8, cudaMemcpyDeviceToHost, s));
   int rc2 = finish(f, s);
   if (!dev) dfree(kk, s);
   return rc ? rc : rc2;

@@ -15,8 +15,12 @@
 //    coordinate 32h + l, an XOR scan across the lanes gives key bits
 //    32h .. 32h+31 of all 32 points at once, and a bit-matrix transpose across
 //    the warp hands each point its 32 key bits.
-//  * general path: each thread forms the top L bits of all d coordinates in
-//    shared memory and runs the transform with L levels.
+//  * general path (the prefix reaches below the top level, L >= 2 levels):
+//    the same bit-sliced idea one level deeper -- the transform runs on
+//    32-point words, one lane per group of 32 points, with the top L planes
+//    sliced and the key words packed by warp transposes (prefix_bitsliced_kernel
+//    below); one thread per point only where a warp's tile would not fit in
+//    shared memory.
 #include <cuda_runtime.h>
 
 #include "hf_internal.cuh"
@@ -123,7 +127,146 @@ __global__ void prefix_sliced_kernel(const uint32_t* __restrict__ p0t, int64_t n
   }
 }
 
-// General path: one thread per point, Y in shared memory.
+// General path (L >= 2 top levels) in bit-sliced form. A warp takes `gpw`
+// point groups (32 points each); lane j owns group g0 + j and keeps one 32-bit
+// word per (level l, permuted coordinate i) -- bit p = level-l bit of
+// coordinate i of point 32(g0 + j) + p -- in row l*d + i of its column of the
+// warp's shared-memory tile (row stride `rs`, odd, so that a row's columns,
+// a column's 32 consecutive rows and any 32 distinct rows of one 32-row span
+// fall in distinct banks). Row l*d + i is also key bit l*d + i from the top,
+// so the packing at the end reads rows in order.
+//
+// Skilling's map on whole words: at level q the points whose coordinate i has
+// bit q set (mask c) invert the lower levels of coordinate 0, the others
+// exchange the lower levels of coordinates 0 and i; with f = x0 ^ xi that is
+// x0 ^= c | f and xi ^= f & ~c on every lower level. The Gray step is a
+// running XOR over the coordinates, and the final correction of level r is
+// the XOR of the last coordinate's levels above r. One lane thus transforms
+// 32 points at once; loading (point-major planes -> sliced words) and packing
+// (sliced words -> point-major key words) are 32 x 32 bit transposes across
+// the warp, one group at a time.
+template <int L>
+__global__ void prefix_bitsliced_kernel(const uint32_t* __restrict__ planes, int64_t n, int d, int W32, int K,
+                                        int gpw, int rs, const int32_t* __restrict__ pi,
+                                        const uint32_t* __restrict__ rbits, uint64_t* __restrict__ pk) {
+  extern __shared__ uint32_t smk[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int rows = L * d;
+  int* inv = reinterpret_cast<int*>(smk);  // inv[pi[i]] = i
+  uint32_t* S = smk + d + (size_t)warp * rows * rs;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) inv[__ldg(pi + i)] = i;
+  __syncthreads();
+  const int64_t G = (n + 31) / 32;
+  const int nhalf = 2 * K;
+  for (int64_t g0 = ((int64_t)blockIdx.x * nwb + warp) * gpw; g0 < G; g0 += (int64_t)gridDim.x * nwb * gpw) {
+    const int ng = (int)(G - g0 < gpw ? G - g0 : gpw);
+    // 1. slice: plane word m of level l for the group's 32 points, transposed,
+    //    leaves coordinate 32m + lane's word in this lane; it goes to the row of
+    //    its permuted position, inverted when that position is reflected. The
+    //    L loads of the next (group, plane word) are in flight meanwhile.
+    const int tasks = ng * W32;
+    uint32_t v[L];
+    auto load = [&](int e, uint32_t* dst) {
+      const int j = e / W32, m = e - j * W32;
+      const int64_t p = (g0 + j) * 32 + lane;
+#pragma unroll
+      for (int l = 0; l < L; ++l) dst[l] = p < n ? __ldg(planes + ((size_t)l * n + p) * W32 + m) : 0u;
+    };
+    load(0, v);
+    for (int e = 0; e < tasks; ++e) {
+      uint32_t nx[L];
+      if (e + 1 < tasks) {
+        load(e + 1, nx);
+      } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l) nx[l] = 0u;
+      }
+      const int j = e / W32, m = e - j * W32;
+      const int c = m * 32 + lane;
+      int i = 0;
+      uint32_t flip = 0u;
+      if (c < d) {
+        i = inv[c];
+        flip = 0u - ((__ldg(rbits + (i >> 5)) >> (i & 31)) & 1u);
+      }
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const uint32_t x = warp_transpose32(v[l], lane);
+        if (c < d) S[(size_t)(l * d + i) * rs + j] = x ^ flip;
+        v[l] = nx[l];
+      }
+    }
+    __syncwarp();
+    // 2. transform column `lane`
+    if (lane < ng) {
+      uint32_t* col = S + lane;
+      uint32_t x0[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) x0[l] = col[(size_t)(l * d) * rs];
+#pragma unroll
+      for (int q = 0; q < L - 1; ++q) {
+        const uint32_t c0 = x0[q];  // coordinate 0 against itself: inversion only
+#pragma unroll
+        for (int r = q + 1; r < L; ++r) x0[r] ^= c0;
+        for (int i = 1; i < d; ++i) {
+          const uint32_t c = col[(size_t)(q * d + i) * rs];
+#pragma unroll
+          for (int r = q + 1; r < L; ++r) {
+            uint32_t* a = col + (size_t)(r * d + i) * rs;
+            const uint32_t xi = *a;
+            const uint32_t f = x0[r] ^ xi;
+            x0[r] ^= c | f;
+            *a = xi ^ (f & ~c);
+          }
+        }
+      }
+      uint32_t run[L], t[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) run[l] = x0[l];
+      for (int i = 1; i < d; ++i) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          uint32_t* a = col + (size_t)(l * d + i) * rs;
+          run[l] ^= *a;
+          *a = run[l];
+        }
+      }
+      uint32_t acc = 0;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        t[l] = acc;
+        acc ^= run[l];
+      }
+#pragma unroll
+      for (int l = 0; l < L; ++l) col[(size_t)(l * d) * rs] = x0[l] ^ t[l];
+      for (int i = 1; i < d; ++i) {
+#pragma unroll
+        for (int l = 1; l < L; ++l) col[(size_t)(l * d + i) * rs] ^= t[l];
+      }
+    }
+    __syncwarp();
+    // 3. pack: half h of group j's key words is rows 32h .. 32h+31 of column
+    //    j, transposed (bit-reversed: most significant bit first)
+    for (int j = 0; j < ng; ++j) {
+      const int64_t p = (g0 + j) * 32 + lane;
+      uint32_t hi = 0;
+      for (int h = 0; h < nhalf; ++h) {
+        const int b = 32 * h + lane;
+        uint32_t x = b < rows ? S[(size_t)b * rs + j] : 0u;
+        x = __brev(warp_transpose32(x, lane));
+        if (h & 1) {
+          if (p < n) pk[(size_t)(h >> 1) * n + p] = ((uint64_t)hi << 32) | x;
+        } else {
+          hi = x;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Per-thread general path: one thread per point, Y in shared memory. Used
+// where the sliced tile of one warp would not fit in shared memory.
 __global__ void prefix_general_kernel(const uint32_t* __restrict__ planes, int64_t n, int d,
                                       int W32, int K, int L, const int32_t* __restrict__ pi,
                                       const uint32_t* __restrict__ rbits,
@@ -173,6 +316,47 @@ void set_smem(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <int L>
+void bitsliced_launch(unsigned blocks, int threads, size_t smem, const uint32_t* planes, int64_t n, int d, int W32,
+                      int K, int gpw, int rs, const int32_t* pi, const uint32_t* rbits, uint64_t* pk, cudaStream_t s) {
+  set_smem((const void*)prefix_bitsliced_kernel<L>, smem);
+  prefix_bitsliced_kernel<L><<<blocks, threads, smem, s>>>(planes, n, d, W32, K, gpw, rs, pi, rbits, pk);
+}
+
+// The bit-sliced general path; false (nothing launched) when one warp's tile
+// does not fit in shared memory. Groups per warp: as few as give about 16
+// warps per SM (the kernel is latency-bound: 8 or 32 per SM measured slower),
+// up to one per lane.
+bool launch_prefix_bitsliced(const uint32_t* planes, int64_t n, int d, int W32, int K, int L, const int32_t* pi,
+                             const uint32_t* rbits, uint64_t* pk, cudaStream_t s) {
+  constexpr int64_t kWarpsWanted = 152 * 16;
+  constexpr size_t kSmemCap = 200 * 1024;
+  const int64_t G = (n + 31) / 32;
+  const int64_t want = (G + kWarpsWanted - 1) / kWarpsWanted;
+  const int gpw = want < 1 ? 1 : (want > 32 ? 32 : (int)want);
+  const int rs = gpw | 1;
+  const size_t per_warp = (size_t)L * d * rs * sizeof(uint32_t);
+  int nwb = 4;
+  while (nwb > 1 && d * sizeof(int) + nwb * per_warp > kSmemCap) nwb >>= 1;
+  const size_t smem = d * sizeof(int) + nwb * per_warp;
+  if (smem > kSmemCap) return false;
+  const int64_t warps = (G + gpw - 1) / gpw;
+  int64_t blocks = (warps + nwb - 1) / nwb;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  const int thr = 32 * nwb;
+  switch (L) {
+    case 2: bitsliced_launch<2>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    case 3: bitsliced_launch<3>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    case 4: bitsliced_launch<4>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    case 5: bitsliced_launch<5>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    case 6: bitsliced_launch<6>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    case 7: bitsliced_launch<7>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+    default: bitsliced_launch<8>((unsigned)blocks, thr, smem, planes, n, d, W32, K, gpw, rs, pi, rbits, pk, s); break;
+  }
+  hf_after_launch("prefix_bitsliced_kernel", s);
+  return true;
+}
+
 }  // namespace
 
 bool prefix_top_path(int d, int K, int L) { return L == 1 && d >= 64 * K; }
@@ -199,6 +383,7 @@ void launch_prefix_keys(const uint32_t* planes, const uint32_t* p0t, int64_t n, 
     hf_after_launch("prefix_sliced_kernel", s);
     return;
   }
+  if (L >= 2 && L <= 8 && launch_prefix_bitsliced(planes, n, d, W32, K, L, pi, rbits, pk, s)) return;
   const int t = threads_for_bytes_per_thread(d);
   const size_t smem = (size_t)t * d;
   set_smem((const void*)prefix_general_kernel, smem);

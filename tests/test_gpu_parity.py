@@ -86,6 +86,38 @@ def test_codes_keys_order_bit_exact(hf, n, d, T, bits, opts):
     G.close()
 
 
+@pytest.mark.parametrize("n,d,bits,opts", [
+    (20000, 16, 8, None),                  # tiny config: 8 levels, 128 bits (every key bit)
+    (200003, 16, 8, None),                 # 32 groups per warp, ragged last warp
+    (4099, 64, 8, None),                   # 2 levels
+    (347001, 64, 8, None),                 # 2 levels, many warps
+    (3001, 33, 5, None),                   # 4 levels, d*b not a multiple of 64
+    (2999, 100, 8, None),                  # 2 levels, 3 words (a settling word), 4 plane words
+    (1500, 127, 3, "prefix_words=2"),      # 2 of 3 levels, coordinates past the first plane word
+    (777, 1, 8, "prefix_words=1"),         # d = 1: all 8 levels in 8 bits
+    (1000, 2, 8, "prefix_words=1"),
+    (1234, 3, 4, "prefix_words=1"),        # key shorter than a word
+    (3000, 7, 2, None),                    # 14-bit keys
+    (999, 31, 8, "prefix_words=4"),        # 8 levels, 4 words
+    (1111, 60, 6, "prefix_words=5"),       # 6 levels, 5 words
+    (500, 100, 8, "prefix_words=8"),       # 8 words from 6 levels
+    (300, 511, 8, "prefix_words=8"),       # 2 levels of 511 coordinates: 16 plane words, 1022 rows
+    (31, 16, 8, None),                     # fewer points than one group
+    (5003, 384, 8, None),                  # top-level path (bit-sliced plane 0)
+    (4001, 128, 8, None),                  # top-level path at d = 128
+])
+def test_prefix_words_bit_exact(hf, n, d, bits, opts):
+    """The sort's prefix words, as the build's key kernels form them, equal
+    the first K2 words of the oracle's full keys, for every tree."""
+    x = S.gaussian_mixture(n, d, n_components=20, seed=S.SEED_DATA) if n > 100 else S.unit_gaussian(n, d, seed=3)
+    G = hf.build(cuda(x), T=3, bits=bits, seed=11, options=opts)
+    F = O.Forest(x, T=3, bits=bits, seed=11)
+    assert 1 <= G.K <= G.K2 <= G.W
+    for t in range(3):
+        assert np.array_equal(G.prefix(t), F.keys[t][:, :G.K2]), f"prefix words of tree {t} (L = {G.L})"
+    G.close()
+
+
 def test_duplicate_points_order(hf):
     """Long runs of equal full keys (exact duplicates) and of equal prefixes."""
     x = S.unit_gaussian(6000, 384, seed=5)
