@@ -30,7 +30,13 @@ namespace {
 
 // 32 x 32 bit-matrix transpose across the warp: lane l holds row l (bit j =
 // entry (l, j)); afterwards lane j holds column j (bit l = entry (l, j)).
-// Stage s swaps the off-diagonal s x s blocks between lanes l and l ^ s.
+// Stage s swaps the off-diagonal s x s blocks between lanes l and l ^ s: a
+// lane keeps the bit positions whose bit s equals its own lane bit s and takes
+// the others from its partner's word moved by s positions -- up for the lower
+// lane, down for the upper one. Both moves are one rotation (by 32 - s or s):
+// the bits that wrap around land only in kept positions. Per stage that is a
+// shuffle, a funnel shift and one three-input logic op; the keep masks and
+// rotation amounts depend on the lane alone.
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
@@ -38,8 +44,11 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 #pragma unroll
     for (int p = 0; p < 32; ++p)
       if (!(p & s)) mlo |= 1u << p;
+    const bool up = (lane & s) != 0;
+    const uint32_t keep = up ? ~mlo : mlo;
     const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
-    x = (lane & s) ? ((x & ~mlo) | ((y & ~mlo) >> s)) : ((x & mlo) | ((y & mlo) << s));
+    const uint32_t moved = __funnelshift_r(y, y, up ? s : 32 - s);
+    x = (x & keep) | (moved & ~keep);
   }
   return x;
 }
