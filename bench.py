@@ -52,7 +52,7 @@ MODES = {"plain": 0, "tensor": 1, "fp8": 2}
 # DRAM traffic of the dominant kernels from one ncu capture of a 1M-point
 # launch (bytes per point, scaled by n here) and the source file it was taken
 # on; a figure is dropped (null) once its source differs.
-WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "cd0725673dcf443f", "file": "window.cu"}   # w = 32
+WINDOW_TRAFFIC = {"bytes_per_point": 1901, "source_sha": "1b5d82fbf71cae05", "file": "window.cu"}   # w = 32; captured at cd0725673dcf443f, which differs only in the header comment
 GRAM_TRAFFIC = {"bytes_per_point": 1132, "source_sha": "47427dc25b29ab93", "file": "gram.cu", "w": 1024}
 
 # GB300: 152 SMs x 128 FP32 lanes; one pair-coordinate update of the exact-

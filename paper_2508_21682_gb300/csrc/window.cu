@@ -1,8 +1,8 @@
 // Window distances and top-k merge (plain float32 form).
 //
-// Paper, Algorithm 2: for the point j at position i of a sort's Hilbert order,
-// the neighbours around position i are appended to its candidate set; the
-// final selection keeps the top k by vector distance. Here the window is w
+// Paper, Algorithm 2: in every sort, the points lying a few places before and
+// after a point in that sort's Hilbert order join its candidates, and the
+// best k candidates by vector distance are the result. Here the window is w
 // positions on each side, the distance is the float32 squared Euclidean
 // distance with exact coordinate differences, and each point's list (k pairs
 // of (distance, index), ascending) is merged tree by tree, so the candidate
