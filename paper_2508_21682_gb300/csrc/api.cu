@@ -1266,11 +1266,22 @@ int hf_debug_prefix(hf_forest* f, int32_t tree, uint64_t* out_words, void* strea
   const bool dev = classify(out_words) == 1;
   uint64_t* kk = dev ? out_words : nullptr;
   if (!dev && dalloc(&kk, cnt, s) != cudaSuccess) return HF_ENOMEM;
-  launch_prefix_keys(f->planes, f->p0t, f->n, f->d, f->bits, f->K2, f->L, f->pi + (size_t)tree * f->d,
+  // the build freed its bit-sliced plane 0; it is made again so that the
+  // words come from the same kernel as in the build
+  uint32_t* p0t = nullptr;
+  if (prefix_top_path(f->d, f->K2, f->L)) {
+    if (dalloc(&p0t, (size_t)((f->n + 31) / 32) * f->d, s) != cudaSuccess) {
+      if (!dev) dfree(kk, s);
+      return HF_ENOMEM;
+    }
+    launch_plane0_slice(f->planes, f->n, f->d, p0t, s);
+  }
+  launch_prefix_keys(f->planes, p0t, f->n, f->d, f->bits, f->K2, f->L, f->pi + (size_t)tree * f->d,
                      f->rbits + (size_t)tree * f->W32, kk, s);
   int rc = HF_OK;
   if (!dev) rc = map_cuda(cudaMemcpyAsync(out_words, kk, cnt * 8, cudaMemcpyDeviceToHost, s));
   int rc2 = finish(f, s);
+  dfree(p0t, s);
   if (!dev) dfree(kk, s);
   return rc ? rc : rc2;
 }
