@@ -10,6 +10,11 @@ adjacency of the curve, the 2-D textbook curve, hand-derived traversals in
 cases, brute-force special cases of the graph and of search, and recall
 monotonicity. Recall values themselves are parity-unpinned against the paper
 (its datasets are not available).
+
+``oracle.c_oracle`` loads a second restatement of the same path in plain C++
+(``hf_oracle.cpp``: scalar loops, compiled without fused multiply-adds). It
+is not imported here; ``tests/test_oracle_cpp.py`` runs the curve pins on it
+and compares it with this numpy oracle element by element.
 """
 from .hilbert_forest import *  # noqa: F401,F403
 from .hilbert_forest import (  # noqa: F401
