@@ -87,3 +87,14 @@ def test_measured_peaks_or_fallback():
     peaks, src = bench.measured_peaks()
     assert src in ("of measured", "of fallback")
     assert float(peaks["hbm_gbs"]) > 0
+
+
+def test_cpp_oracle_baseline_on_a_tiny_sample():
+    """The C++ oracle's share of the CPU baseline: threads x sample points per
+    second of wall time, scaled from the sample's trees to the workload's."""
+    class A:
+        n, d, T, w, k, nq, search_w, components, bits = 100_000, 8, 16, 4, 5, 1000, 4, 5, 8
+
+    val, wall = bench.cpp_oracle_parallel(A, 2, 200, 1)
+    assert wall > 0
+    assert val == pytest.approx(2 * 200 / (wall * 16))
