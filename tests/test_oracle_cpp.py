@@ -170,3 +170,69 @@ def test_cpp_full_grid_order_is_the_curve():
         order = np.lexsort([keys[:, w] for w in range(keys.shape[1] - 1, -1, -1)])
         steps = np.abs(np.diff(pts[order], axis=0)).sum(axis=1)
         assert np.all(steps == 1)
+
+
+# ---------------------------------------------------------------- planted mistakes
+MUTATIONS = {
+    "no_gray": ("for (int i = 1; i < d; ++i) X[i] ^= X[i - 1];", ""),
+    "no_t": ("for (int i = 0; i < d; ++i) X[i] ^= t;", ""),
+    "t_from_x0": ("if ((X[d - 1] >> q) & 1u) t ^= (1u << q) - 1u;", "if ((X[0] >> q) & 1u) t ^= (1u << q) - 1u;"),
+    "invert_too_many": ("X[0] ^= P;", "X[0] ^= (P << 1) | 1u;"),
+    "no_exchange_back": ("X[0] ^= t;\n        X[i] ^= t;", "X[0] ^= t;"),
+    "levels_upward": ("for (int q = bits - 1; q >= 1; --q) {\n    const uint32_t P", "for (int q = 1; q <= bits - 1; ++q) {\n    const uint32_t P"),
+}
+
+
+def mutant_transpose(tmp_path, name):
+    """The C++ oracle's own source with one planted mistake, compiled apart."""
+    import ctypes
+    import subprocess
+
+    old, new = MUTATIONS[name]
+    src = open(C.SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.cpp"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.run(["g++", *C.FLAGS, "-o", str(so), str(path)], check=True, capture_output=True)
+    L = ctypes.CDLL(str(so))
+    L.hfo_transpose.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    L.hfo_transpose.restype = None
+
+    def f(coords, bits):
+        c = np.ascontiguousarray(coords, dtype=np.uint32)
+        X = np.empty_like(c)
+        L.hfo_transpose(c.ctypes.data, c.shape[0], c.shape[1], bits, X.ctypes.data)
+        return X
+
+    return f
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_cpp_pins_catch_planted_mistakes(tmp_path, name):
+    f = mutant_transpose(tmp_path, name)
+    caught = not check_curve(f, dims=(2, 3), bits=(2, 3)) or not all(
+        self_similar(f, d, b) for d, b in [(2, 3), (3, 2), (3, 3)])
+    assert caught, name
+
+
+def test_cpp_pack_pin_catches_reversed_bit_order(tmp_path):
+    """The hand-packed layout pin fails for a key packed least significant
+    bit first."""
+    import ctypes
+    import subprocess
+
+    src = open(C.SRC).read()
+    old = "key[g / 64] |= bit << (63 - g % 64);"
+    assert src.count(old) == 1
+    path = tmp_path / "pack.cpp"
+    path.write_text(src.replace(old, "key[g / 64] |= bit << (g % 64);"))
+    so = tmp_path / "pack.so"
+    subprocess.run(["g++", *C.FLAGS, "-o", str(so), str(path)], check=True, capture_output=True)
+    L = ctypes.CDLL(str(so))
+    L.hfo_pack_key.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    L.hfo_pack_key.restype = None
+    X = np.array([[2, 1]], np.uint32)
+    out = np.empty((1, 1), np.uint64)
+    L.hfo_pack_key(X.ctypes.data, 1, 2, 2, out.ctypes.data)
+    assert int(out[0, 0]) != 0b1001 << 60
