@@ -236,3 +236,14 @@ def test_cpp_pack_pin_catches_reversed_bit_order(tmp_path):
     out = np.empty((1, 1), np.uint64)
     L.hfo_pack_key(X.ctypes.data, 1, 2, 2, out.ctypes.data)
     assert int(out[0, 0]) != 0b1001 << 60
+
+
+def test_cpp_equals_numpy_on_the_tiny_configuration():
+    """The tiny configuration in full (20,000 x 16 unit Gaussian, T = 8, b = 8,
+    w = 16, k = 10): both oracles give the same orders and the same graph."""
+    x = S.unit_gaussian(20_000, 16, seed=S.SEED_DATA)
+    Fc = C.Forest(x, T=8, bits=8, seed=S.SEED_FOREST)
+    Fn = O.Forest(x, T=8, bits=8, seed=S.SEED_FOREST)
+    for t in range(8):
+        assert np.array_equal(Fc.sigma[t], Fn.sigma[t])
+    same_lists(*C.knn_graph(Fc, 10, 16), *O.knn_graph(Fn, 10, 16))
