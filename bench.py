@@ -322,20 +322,28 @@ def run_ours(a):
     gdh = torch.empty((n, k), dtype=torch.float32).pin_memory()
     sih = torch.empty((a.nq, k), dtype=torch.int32).pin_memory()
     sdh = torch.empty((a.nq, k), dtype=torch.float32).pin_memory()
-    e2e_ms = []
+    e2e_ms, e2e_calls = [], []
     for i in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G = hf.build(xh, T=T, bits=a.bits, seed=3)
+        t1 = time.perf_counter()
         if a.mode != "plain":
             G.set_option("mode", MODES[a.mode])
             G.set_option("tensor_slack", a.tensor_slack)
         G.knn_graph(k, w, gih, gdh)
+        t2 = time.perf_counter()
         G.search(qh, k, a.search_w, sih, sdh)
+        t3 = time.perf_counter()
         G.close()
         torch.cuda.synchronize()
+        t4 = time.perf_counter()
         if i:  # first one is a warm-up
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_ms.append((t4 - t0) * 1e3)
+            # each call returns only after its stream has drained, so these
+            # wall-clock spans are the calls' own
+            e2e_calls.append({"build": (t1 - t0) * 1e3, "graph": (t2 - t1) * 1e3, "search": (t3 - t2) * 1e3,
+                              "close": (t4 - t3) * 1e3})
     e2e_step = max_over_ranks(statistics.mean(e2e_ms) if e2e_ms else float("nan"), dist, dev)
 
     # plain float32 mode beside it (outside the timed region)
@@ -430,7 +438,9 @@ def run_ours(a):
             "e2e": {"value": job_value(ws, n, e2e_step), "unit": "points/s",
                     "h2d_bytes_per_step": int(x.nbytes + q.nbytes),
                     "d2h_bytes_per_step": int(gih.numel() * 4 + gdh.numel() * 4 + sih.numel() * 4 + sdh.numel() * 4),
-                    "ms_per_step": e2e_step},
+                    "ms_per_step": e2e_step,
+                    "calls_ms": {c: statistics.mean(r[c] for r in e2e_calls) for c in e2e_calls[0]}
+                    if e2e_calls else None},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cpu,
