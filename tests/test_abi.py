@@ -72,6 +72,8 @@ def test_invalid_arguments_rejected_before_any_device_work(hf):
     assert L.hf_free(None) == hf.HF_OK
     assert L.hf_tree_params(0, 0, 0, p, p) == hf.HF_EINVAL
     assert L.hf_debug_keys_from_codes(p, 0, 3, 8, p, None) == hf.HF_EINVAL
+    assert L.hf_debug_prefix(None, 0, p, None) == hf.HF_EINVAL
+    assert L.hf_info(None, p, 8) == hf.HF_EINVAL
 
 
 def test_product_path_fails_loudly_without_library(hf, monkeypatch, tmp_path):
